@@ -1,0 +1,356 @@
+#!/usr/bin/env python
+"""Throughput of the swift left inverse x~ = Zh^- x on B300 (one JSON line).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload NAME]
+
+A step is one application of the left inverse to one batch of R right-hand
+sides of the named workload (default: 256 x 256 periodic grid x 32 levels,
+K = 64 members, L = 949 kept modes, R = 64 per batch, mixed precision), with
+the inputs already resident in HBM.  The metric is right-hand-side vectors per
+second (setup excluded; it is reported separately).  Under torchrun every rank
+runs an independent replica on its own batch (the right-hand sides are
+independent problems): weak scaling, no collective on the data path; the time
+is the max over ranks.
+
+--impl reference times the FP64 CPU oracle (the only other implementation of
+this method) on the host cores, one right-hand side per step.
+"""
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2609_13327_b300 import synth  # noqa: E402
+
+DEFAULT_WORKLOAD = "c3_256x256x32"
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(synth.WORKLOADS))
+    ap.add_argument("--prec", default=None, choices=["fp64", "fp32", "mixed"])
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ----------------------------------------------------------------------------- bytes and peaks
+
+def element_sizes(prec):
+    """(s_x, s_z): bytes per state/coefficient element and per ensemble element.
+
+    The mixed-precision workload fixes the ensemble operand at 2 bytes (BF16 class)."""
+    if prec == "fp64":
+        return 8, 8
+    if prec == "mixed":
+        return 4, 2
+    return 4, 4
+
+
+def algorithmic_bytes_per_rhs(w, L, prec, R):
+    """Read x once, write x~ once, read the ensemble once per batch of R."""
+    sx, sz = element_sizes(prec)
+    return sx * (w.n + w.K * L) + sz * w.n * w.K / R
+
+
+def measured_peak_hbm():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+def kernel_sources_sha(files):
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel, workload, prec):
+    """DRAM bytes per launch from a committed ncu summary, if the kernel has not changed since."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            table = json.load(f)
+    except Exception:
+        return None
+    for e in table:
+        if e.get("kernel") == kernel and e.get("workload") == workload and e.get("prec") == prec:
+            if e.get("sources_sha") == kernel_sources_sha(e.get("sources", [])):
+                return e.get("dram_bytes_per_launch")
+    return None
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid=None):
+        self.file = tempfile.NamedTemporaryFile(mode="w+", suffix=".csv", delete=False)
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "20"]
+        if uuid:
+            cmd.insert(1, f"--id={uuid}")
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [r.split(",") for r in self.file.read().strip().splitlines() if r.count(",") >= 8]
+        self.file.close()
+        os.unlink(self.file.name)
+        return rows
+
+    @staticmethod
+    def summarize(rows, t_start, t_stop):
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[5 + i] and "Not" not in r[5 + i]})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------- CPU oracle timing
+
+def blas_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        n = [i.get("num_threads", 1) for i in threadpool_info() if i.get("user_api") == "blas"]
+        return max(n) if n else 1
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def oracle_plan(w, prec):
+    from oracle import basis, swift
+    Z = synth.ensemble(w).astype(synth.storage_dtype(prec)).astype(np.float64)
+    lam = basis.spectrum_2d(w.Nx, w.Ny, w.ell_loc)
+    t0 = time.perf_counter()
+    plan = swift.Plan(Z, w.Nx, w.Ny, lam, w.tau)
+    return plan, time.perf_counter() - t0
+
+
+def cpu_baseline(w, prec, nrhs=8):
+    """The oracle as it stands, on the host cores: setup untimed, then nrhs right-hand sides."""
+    from oracle import swift
+    plan, t_setup = oracle_plan(w, prec)
+    x = synth.rhs(w, R=nrhs, dtype=synth.storage_dtype(prec)).astype(np.float64)
+    swift.apply_left_inverse(plan, x[:1])
+    t0 = time.perf_counter()
+    swift.apply_left_inverse(plan, x)
+    dt = time.perf_counter() - t0
+    return {"value": nrhs / dt, "unit": "vectors/s", "cores": blas_threads(), "kind": "oracle",
+            "sample": f"{nrhs} right-hand sides of the full {w.name} workload through the FP64 NumPy oracle "
+                      f"(setup {t_setup:.1f} s, excluded like the GPU setup)"}
+
+
+def run_reference(args, w, prec):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from oracle import swift
+    plan, t_setup = oracle_plan(w, prec)
+    L = plan.L
+    x = synth.rhs(w, R=1, dtype=synth.storage_dtype(prec)).astype(np.float64)
+    for _ in range(args.warmup):
+        swift.apply_left_inverse(plan, x)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        swift.apply_left_inverse(plan, x)
+    dt = time.perf_counter() - t0
+    value = args.steps / dt
+    cores = blas_threads()
+    line = {
+        "impl": "reference", "metric": "left-inverse applications/s", "value": value, "unit": "vectors/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(w, L, prec, 1),
+        "cpu_baseline": {"value": value, "unit": "vectors/s", "cores": cores, "kind": "oracle",
+                         "sample": f"one right-hand side of {w.name} per step (FP64 NumPy oracle, "
+                                   f"setup {t_setup:.1f} s excluded)"},
+        "e2e": {"value": value, "unit": "vectors/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- GPU arm
+
+def workload_config(w, L, prec, R):
+    return {"workload": f"{w.name}: {w.Nx}x{w.Ny} periodic grid x {w.nw} levels, K={w.K} members, "
+                        f"L={L} kept modes, {R} right-hand sides per step, {prec}",
+            "nx": w.Nx, "ny": w.Ny, "nw": w.nw, "K": w.K, "L": L, "rhs_per_step": R, "prec": prec,
+            "tau": w.tau, "ell_loc": w.ell_loc,
+            "l2": "no flush: every step reads a different-order stream of x larger than the 126 MB L2"}
+
+
+def run_ours(args, w, prec):
+    import torch
+    world, rank, local = dist_env()
+    from paper_2609_13327_b300 import zl
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    R = w.R
+    sdt = synth.storage_dtype(prec)
+
+    Z = torch.from_numpy(synth.ensemble(w).astype(sdt)).to(dev)
+    lam = zl.zl_gaussian_spectrum(w.Nx, w.Ny, w.ell_loc)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plan = zl.zl_setup(Z, lam, tau=w.tau, prec=prec, max_rhs=R, nx=w.Nx, ny=w.Ny)
+    setup_s = time.perf_counter() - t0
+    del Z
+    x = torch.from_numpy(synth.rhs(w, R=R, seed=w.seed + 1000 * rank, dtype=sdt)).to(dev)
+    out = torch.empty((R, w.K, plan.L), dtype=x.dtype, device=dev)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(max(args.warmup, 3)):
+        zl.zl_apply_left_inverse(plan, x, out, stream)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(local).uuid)
+        uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+    except Exception:
+        pass
+    sampler = ClockSampler(uuid)
+    time.sleep(0.3)
+    barrier()
+    plan.set_stage_timing(True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t_wall0 = time.time()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        zl.zl_apply_left_inverse(plan, x, out, stream)
+    ev1.record(stream)
+    barrier()
+    t_wall1 = time.time()
+    plan.set_stage_timing(False)
+    rows = sampler.stop()
+    ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        tt = torch.tensor([ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        ms = float(tt.item())
+    stages = plan.stage_times()
+    launches = sum(n for n, _ in stages.values())
+    value = world * args.steps * R / (ms / 1e3)
+
+    # dominant kernel: the column/x-pass stage
+    n_col, ms_col = stages["fwd_column"]
+    avg_col_s = ms_col / max(n_col, 1) / 1e3
+    bpr = algorithmic_bytes_per_rhs(w, plan.L, prec, R)
+    peak, peak_kind = measured_peak_hbm()
+    achieved = bpr * R / avg_col_s / 1e9
+    kernel_name = "zl_fwd_column_tc" if (prec == "mixed" and plan_uses_tc(plan)) else "fwd_column_xpass"
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": recorded_traffic(kernel_name, w.name, prec), "kernel": kernel_name,
+                "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback",
+                "kernel_ms_per_launch": avg_col_s * 1e3,
+                "step_frac": bpr * R / (ms / args.steps / 1e3) / 1e9 / peak,
+                "stages_ms_per_launch": {k: (v[1] / v[0] if v[0] else None) for k, v in stages.items()}}
+
+    # end to end through the host-buffer entry point: H2D of x and D2H of x~ inside every step
+    xh = x.cpu().pin_memory()
+    oh = torch.empty((R, w.K, plan.L), dtype=x.dtype).pin_memory()
+    zl.zl_apply_left_inverse_host(plan, xh, oh, stream)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        zl.zl_apply_left_inverse_host(plan, xh, oh, stream)
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        tt = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    e2e = {"value": world * args.e2e_steps * R / e2e_s, "unit": "vectors/s",
+           "h2d_bytes_per_step": xh.numel() * xh.element_size(), "d2h_bytes_per_step": oh.numel() * oh.element_size(),
+           "steps": args.e2e_steps, "api": "zl_apply_left_inverse_host (pinned host buffers)"}
+
+    clocks = ClockSampler.summarize(rows, t_wall0, t_wall1)
+    line = {
+        "metric": "left-inverse applications/s", "value": value, "unit": "vectors/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f16x3 split, f32 accumulate" if (prec == "mixed" and plan_uses_tc(plan)) else
+                 ("f64" if prec == "fp64" else "f32"),
+        "data": "synthetic (seeded Gaussian-correlated ensemble, N(0,1) right-hand sides)",
+        "config": workload_config(w, plan.L, prec, R), "setup_s": setup_s,
+        "roofline": roofline, "clocks": clocks, "e2e": e2e, "gpu_launches": launches,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w, prec)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.destroy()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def plan_uses_tc(plan):
+    return getattr(plan, "uses_tc", lambda: False)()
+
+
+def main():
+    args = parse_args()
+    w = synth.WORKLOADS[args.workload]
+    prec = args.prec or w.prec
+    if args.impl == "reference":
+        run_reference(args, w, prec)
+    else:
+        run_ours(args, w, prec)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,209 @@
+/*
+ * zl.h -- C ABI of libzl: the swift left inverse of the square root of a
+ * horizontally localized ensemble covariance, on one NVIDIA B300 (sm_103a).
+ *
+ * Method: Sardelli & Bishop, "A swift algorithm to calculate the left inverse
+ * of a square root of a horizontally localized climatological ensemble
+ * covariance matrix" (arxiv 2609.13327).
+ *
+ * Notation (the paper's):
+ *   n_h = nx*ny grid columns (index m = y*nx + x), n_w variables per column
+ *   (levels x kinds, index l), K members (index k), n = n_w*n_h.
+ *   Z     the scaled ensemble z_k = (e_k - mean)/sqrt(K-1) (Sec. 3.3), stored
+ *         [K][n_w][n_h]: member-major, then segment l, then column m (the
+ *         segment ordering of Sec. 3.4).
+ *   C_b   the n_h x n_h horizontal localization block (Sec. 3.5); every block
+ *         of the localization equals C_b.  libzl accepts the localizations
+ *         diagonalised by the packed real-Fourier basis of a periodic grid
+ *         (circulant in 1-D, block-circulant with circulant blocks in 2-D,
+ *         even in each axis): the caller gives their eigenvalues.
+ *   Zh    = C^{1/2} (triangle) Z = A V Delta^{1/2}, the modulated-ensemble
+ *         square root (Sec. 3.6, 3.8), n x K*L.
+ *   Zh^-  = Delta^{-1/2} V^T A^{-1}, its left inverse (Sec. 3.8, Eq.
+ *         InverseSquareRootAlmost).  When n_w != K, A^{-1} is replaced by the
+ *         pseudo-inverse A^+ = blockdiag over columns of A_m^+ (minimum norm
+ *         for n_w < K, least squares for n_w > K); this is a genuine left
+ *         inverse iff n_w >= K.
+ *
+ * Packed real-Fourier basis (per axis of length N; s = p_y*nx + p_x in 2-D):
+ *   b_0 = 1/sqrt(N); b_{2j-1}(m) = sqrt(2/N) cos(2 pi j m/N);
+ *   b_{2j}(m) = sqrt(2/N) sin(2 pi j m/N); b_{N-1}(m) = (-1)^m/sqrt(N) if N even.
+ *
+ * Conventions for every entry point:
+ *   - Device pointers are raw CUDA device addresses, owned by the caller; libzl
+ *     never frees them.  Host pointers are plain host memory.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Applies are stream-ordered and asynchronous; nothing in an
+ *     apply allocates memory or synchronises the host, except the *_host
+ *     variant, which synchronises `stream` before returning.
+ *   - Element type follows the plan's precision: double for ZL_FP64, float for
+ *     ZL_FP32 and ZL_MIXED (tensor-core operands are internal only).
+ *   - No exception or exit crosses the ABI.  Argument errors are detected
+ *     before any work is queued, so output buffers are untouched when an
+ *     entry point returns ZL_ERR_ARG or ZL_ERR_SHAPE.
+ */
+#ifndef ZL_H
+#define ZL_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct zl_plan_s* zl_plan;   /* opaque; owned by libzl, freed by zl_destroy */
+
+typedef enum {
+    ZL_OK = 0,
+    ZL_ERR_ARG = 1,          /* null pointer, bad enum, non-finite or negative parameter   */
+    ZL_ERR_SHAPE = 2,        /* a size outside the supported range                          */
+    ZL_ERR_RANK = 3,         /* some A_m is rank-deficient (Gram pivot test), see get_info   */
+    ZL_ERR_ALLOC = 4,        /* cudaMalloc failed during setup                              */
+    ZL_ERR_CUDA = 5,         /* a CUDA runtime call or kernel launch failed                 */
+    ZL_ERR_TIMEOUT = 6,      /* a bounded device-side wait gave up                          */
+    ZL_ERR_UNSUPPORTED = 7   /* valid request that this build does not implement           */
+} zl_status;
+
+typedef enum {
+    ZL_FP64 = 0,   /* FP64 throughout: the plain GPU form of the algorithm                  */
+    ZL_FP32 = 1,   /* FP32 CUDA-core arithmetic, FP64 setup                                 */
+    ZL_MIXED = 2   /* left inverse on tcgen05 tensor cores (FP16 hi/lo operand splits,
+                      FP32 accumulation), FP64 setup; other operators as ZL_FP32            */
+} zl_precision;
+
+typedef struct {
+    int nx;             /* grid points along x (>= 1)                                        */
+    int ny;             /* grid points along y (>= 1; 1 for a ring)                          */
+    int nw;             /* variables per vertical column n_w = n_G * n_v (>= 1)              */
+    int K;              /* ensemble members (>= 1)                                           */
+    zl_precision prec;
+    double tau;         /* keep mode s iff lambda_s > tau * max(lambda); tau >= 0            */
+    int max_rhs;        /* right-hand sides per internal pass (workspace size); >= 1        */
+} zl_desc;
+
+/*
+ * zl_setup -- precompute everything the applies need (the paper's experiment
+ * steps (a)-(e), Sec. 4.5, and the economical eigendecomposition of C_b,
+ * Sec. 3.8).
+ *
+ *   desc      sizes and precision (copied).
+ *   Z         device, [K][nw][ny*nx], double (ZL_FP64) or float; read only
+ *             during the call (libzl keeps its own copy).
+ *   spectrum  host, [ny*nx] doubles: eigenvalue of C_b for every packed mode s,
+ *             all finite, max > 0.  Modes with lambda_s <= tau*max are dropped
+ *             ("non-zero eigenvalues", Sec. 3.8); L = number kept.
+ *   stream    queue for the setup work; the call synchronises it.
+ *   out       receives the plan.  On ZL_OK and on ZL_ERR_RANK *out is a valid
+ *             plan (on ZL_ERR_RANK every apply returns ZL_ERR_RANK; query the
+ *             first rank-deficient column with zl_get_info, then zl_destroy).
+ *             On any other error *out is NULL.
+ *
+ * Per column m the plan holds the pseudo-inverse A_m^+ (K x n_w), formed in
+ * FP64 from the Gram matrix G_m = A_m A_m^T (n_w <= K) or A_m^T A_m (n_w > K),
+ * its Cholesky factor, and one Newton step P <- P (2I - A_m P) (resp.
+ * (2I - P A_m) P) whose residual is formed in FP64.  Column m is
+ * rank-deficient when a Cholesky pivot is <= 1e-13 * trace(G_m) (rank(A) =
+ * sum_m rank(A_m), supporting information S2).
+ */
+zl_status zl_setup(const zl_desc* desc, const void* Z, const double* spectrum,
+                   void* stream, zl_plan* out);
+
+/*
+ * zl_get_info -- sizes of a plan.  Any output pointer may be NULL.
+ *   L           kept modes; nw, K, nh as in the descriptor;
+ *   bad_column  first rank-deficient column, or -1.
+ */
+zl_status zl_get_info(zl_plan plan, int* L, int* nw, int* K, long long* nh, int* bad_column);
+
+/*
+ * zl_get_modes -- the kept packed mode indices s (ascending), host int[L].
+ * Output coefficient j of every member refers to mode modes[j].
+ */
+zl_status zl_get_modes(zl_plan plan, int* modes);
+
+/*
+ * zl_apply_left_inverse -- x~ = Zh^- x for R state vectors: steps V1-V5 of
+ * Sec. 3.9.  V1: w^(m) = A_m^+ x^(m) for every column; V2-V3: regroup w into
+ * its K member segments; V4: x~_k = Delta_b^{-1/2} V_b^T w_k; V5: concatenate.
+ *
+ *   x    device, [R][nw][ny*nx] (segment order), read only.
+ *   xt   device, [R][K][L], written; may not alias x.
+ *   R    >= 0 (0 is a no-op); any R, processed in passes of max_rhs.
+ */
+zl_status zl_apply_left_inverse(zl_plan plan, const void* x, void* xt, int R, void* stream);
+
+/*
+ * zl_apply_left_inverse_host -- the same operator on HOST buffers: copies x to
+ * the device, applies, copies x~ back, and synchronises `stream`.  x and xt
+ * should be page-locked for the copies to be asynchronous.  The device staging
+ * buffers are owned by the plan and allocated on first use (this is the only
+ * entry point that may allocate after setup).
+ */
+zl_status zl_apply_left_inverse_host(zl_plan plan, const void* x, void* xt, int R, void* stream);
+
+/*
+ * zl_apply_sqrt -- x = Zh x~ = A V Delta^{1/2} x~ (Sec. 3.8):
+ * y_k = V_b Delta_b^{1/2} x~_k, then x^(m) = A_m y^(m) per column.
+ *   xt device [R][K][L] read only;  x device [R][nw][ny*nx] written.
+ */
+zl_status zl_apply_sqrt(zl_plan plan, const void* xt, void* x, int R, void* stream);
+
+/*
+ * zl_apply_adjoint -- g = (Zh^-)^T y = (A^+)^T V Delta^{-1/2} y, the transpose
+ * of Eq. InverseSquareRootAlmost: v_k = V_b Delta_b^{-1/2} y_k, then
+ * g^(m) = (A_m^+)^T v^(m) per column.  This is the gradient map of
+ * J(x) = 1/2 ||Zh^- x||^2: grad J = zl_apply_adjoint(zl_apply_left_inverse(x)).
+ *   y device [R][K][L] read only;  g device [R][nw][ny*nx] written.
+ */
+zl_status zl_apply_adjoint(zl_plan plan, const void* y, void* g, int R, void* stream);
+
+/*
+ * zl_apply_sqrt_adjoint -- t = Zh^T x = Delta^{1/2} V^T A^T x.
+ *   x device [R][nw][ny*nx] read only;  t device [R][K][L] written.
+ */
+zl_status zl_apply_sqrt_adjoint(zl_plan plan, const void* x, void* t, int R, void* stream);
+
+/*
+ * Stage timing (profiling aid).  Each apply runs two kernel stages:
+ *   ZL_STAGE_FWD_COLUMN  per-column product fused with the x-pass of V_b^T
+ *                        (left inverse and Zh^T; the dominant kernel)
+ *   ZL_STAGE_FWD_YPASS   y-pass of V_b^T, Delta scaling, compaction to [K][L]
+ *   ZL_STAGE_INV_YPASS   scaling and y-pass of V_b (square root and adjoint)
+ *   ZL_STAGE_INV_COLUMN  x-pass of V_b fused with the per-column product
+ * While timing is enabled every stage launch is bracketed by two CUDA events
+ * recorded on the launching stream (the events are created on demand).
+ * zl_set_stage_timing(plan, 1) clears earlier records; (plan, 0) stops
+ * recording and keeps them.  zl_get_stage_times waits for the recorded events
+ * and returns the number of launches and their summed duration.
+ */
+typedef enum {
+    ZL_STAGE_FWD_COLUMN = 0,
+    ZL_STAGE_FWD_YPASS = 1,
+    ZL_STAGE_INV_YPASS = 2,
+    ZL_STAGE_INV_COLUMN = 3,
+    ZL_NUM_STAGES = 4
+} zl_stage;
+
+zl_status zl_set_stage_timing(zl_plan plan, int enable);
+zl_status zl_get_stage_times(zl_plan plan, int stage, int* launches, double* total_ms);
+
+/* zl_destroy -- free a plan and everything it owns (NULL is a no-op).  The
+ * caller must make sure no queued apply still uses it. */
+zl_status zl_destroy(zl_plan plan);
+
+/* zl_status_string -- static, human-readable name of a status code. */
+const char* zl_status_string(zl_status s);
+
+/*
+ * zl_gaussian_spectrum -- host helper: eigenvalues, in packed order s =
+ * p_y*nx + p_x, of the separable periodized Gaussian localization
+ * c(d) = sum_p exp(-(d+pN)^2/(2 ell^2)) / sum_p exp(-(pN)^2/(2 ell^2)) per axis
+ * (unit diagonal, as Sec. 2 and Sec. 4.4 require of a localization):
+ * lambda(s) = lambda_x(f(p_x)) * lambda_y(f(p_y)),
+ * lambda_axis(f) = sum_{d<N} c(d) cos(2 pi f d / N).
+ *   out  host, double[nx*ny].
+ */
+zl_status zl_gaussian_spectrum(int nx, int ny, double ell, double* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ZL_H */

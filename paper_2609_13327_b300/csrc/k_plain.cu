@@ -1,0 +1,275 @@
+// CUDA-core kernels of the four operators, templated on the element type
+// (double: the plain FP64 GPU form of the algorithm; float: the FP32 path).
+//
+// All four operators share two shapes.  With M a member matrix stored
+// [K][n_w][n_h] (the ensemble Z, or the per-column pseudo-inverse P) and a
+// per-mode scale (Delta_b^{-1/2} or Delta_b^{1/2}):
+//
+//   forward  out[r][k][j] = scale_j * (V_b^T w_k)_{s_j},  w_k[m] = sum_l M[k][l][m] x[r][l][m]
+//            left inverse (M = P, Delta^{-1/2}): steps V1-V5 of Sec. 3.9
+//            Zh^T         (M = Z, Delta^{+1/2})
+//   inverse  out[r][l][m] = sum_k M[k][l][m] y_k[m],  y_k = V_b (scale (.) c_k)
+//            square root  (M = Z, Delta^{+1/2}): A V Delta^{1/2} (Sec. 3.8)
+//            adjoint      (M = P, Delta^{-1/2}): (A^+)^T V Delta^{-1/2}
+//
+// V_b^T is applied separably: an x-pass per grid row that keeps only the Px
+// x-frequencies that occur among the kept modes (intermediate t1 [R][K][ny][Px]
+// in HBM), then a y-pass that forms each kept mode (p_y, p_x) and scales it.
+// The x-pass is fused with the per-column product: a CTA owns one grid row, so
+// the regrouping of w^(m) into member segments (steps V2-V3, the paper's
+// inter-processor exchange) never leaves shared memory.
+
+#include "zl_internal.cuh"
+
+namespace zl {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int KC = 8;                    // members per CTA in the forward pass
+constexpr size_t kRowSmemBudget = 64 * 1024;
+
+// ---------------------------------------------------------------------------
+// forward, pass 1: per-column product + x-pass, CTA = (grid row y, RC rhs, KC members)
+// ---------------------------------------------------------------------------
+template <typename T, int RC>
+__global__ void __launch_bounds__(kThreads)
+fwd_column_xpass(const T* __restrict__ x, const T* __restrict__ M, const T* __restrict__ bx, T* __restrict__ t1,
+                 int R, int nw, int K, int nx, int ny, int Px) {
+    extern __shared__ unsigned char smem_raw[];
+    T* W = reinterpret_cast<T*>(smem_raw);   // [KC][RC][nx]
+    // member chunk fastest, then rhs chunk, then grid row: the CTAs that share a
+    // row's x and M tiles run back to back and find them in L2
+    const int k0 = blockIdx.x * KC;
+    const int r0 = blockIdx.y * RC;
+    const int y = blockIdx.z;
+    const long long nh = (long long)nx * ny;
+
+    for (int xc = threadIdx.x; xc < nx; xc += blockDim.x) {
+        const long long m = (long long)y * nx + xc;
+        T acc[RC][KC];
+#pragma unroll
+        for (int r = 0; r < RC; ++r)
+#pragma unroll
+            for (int k = 0; k < KC; ++k) acc[r][k] = T(0);
+        for (int l = 0; l < nw; ++l) {
+            T xv[RC];
+#pragma unroll
+            for (int r = 0; r < RC; ++r)
+                xv[r] = (r0 + r < R) ? x[((long long)(r0 + r) * nw + l) * nh + m] : T(0);
+#pragma unroll
+            for (int k = 0; k < KC; ++k) {
+                const T pv = (k0 + k < K) ? M[((long long)(k0 + k) * nw + l) * nh + m] : T(0);
+#pragma unroll
+                for (int r = 0; r < RC; ++r) acc[r][k] = fma(pv, xv[r], acc[r][k]);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < KC; ++k)
+#pragma unroll
+            for (int r = 0; r < RC; ++r) W[((size_t)k * RC + r) * nx + xc] = acc[r][k];
+    }
+    __syncthreads();
+
+    // x-pass: t1[r][k][y][jx] = sum_x W[k][r][x] * bx[jx][x]
+    const int nout = KC * RC * Px;
+    for (int o = threadIdx.x; o < nout; o += blockDim.x) {
+        const int jx = o % Px;
+        const int kr = o / Px;
+        const int r = kr % RC, k = kr / RC;
+        if (r0 + r >= R || k0 + k >= K) continue;
+        const T* w = W + ((size_t)k * RC + r) * nx;
+        const T* b = bx + (size_t)jx * nx;
+        T s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+        int xc = 0;
+        for (; xc + 3 < nx; xc += 4) {
+            s0 = fma(w[xc], b[xc], s0);
+            s1 = fma(w[xc + 1], b[xc + 1], s1);
+            s2 = fma(w[xc + 2], b[xc + 2], s2);
+            s3 = fma(w[xc + 3], b[xc + 3], s3);
+        }
+        for (; xc < nx; ++xc) s0 = fma(w[xc], b[xc], s0);
+        t1[(((long long)(r0 + r) * K + k0 + k) * ny + y) * Px + jx] = (s0 + s1) + (s2 + s3);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// forward, pass 2: y-pass + scale + compaction, CTA = (member k, rhs r)
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+fwd_ypass(const T* __restrict__ t1, const T* __restrict__ by, const int* __restrict__ m_py,
+          const int* __restrict__ m_jx, const T* __restrict__ scale, T* __restrict__ out,
+          int K, int ny, int Px, int L, int ychunk) {
+    extern __shared__ unsigned char smem_raw[];
+    T* acc = reinterpret_cast<T*>(smem_raw);   // [L]
+    T* tile = acc + L;                         // [Px][ychunk]
+    const int k = blockIdx.x, r = blockIdx.y;
+    const T* src = t1 + ((long long)r * K + k) * ny * Px;
+    for (int j = threadIdx.x; j < L; j += blockDim.x) acc[j] = T(0);
+    for (int y0 = 0; y0 < ny; y0 += ychunk) {
+        const int yn = min(ychunk, ny - y0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < yn * Px; e += blockDim.x) {
+            const int yy = e / Px, jx = e - yy * Px;
+            tile[jx * ychunk + yy] = src[(long long)(y0 + yy) * Px + jx];
+        }
+        __syncthreads();
+        for (int j = threadIdx.x; j < L; j += blockDim.x) {
+            const T* b = by + (size_t)m_py[j] * ny + y0;
+            const T* t = tile + (size_t)m_jx[j] * ychunk;
+            T s0 = 0, s1 = 0;
+            int yy = 0;
+            for (; yy + 1 < yn; yy += 2) {
+                s0 = fma(b[yy], t[yy], s0);
+                s1 = fma(b[yy + 1], t[yy + 1], s1);
+            }
+            if (yy < yn) s0 = fma(b[yy], t[yy], s0);
+            acc[j] += s0 + s1;
+        }
+    }
+    __syncthreads();
+    T* o = out + ((long long)r * K + k) * L;
+    for (int j = threadIdx.x; j < L; j += blockDim.x) o[j] = acc[j] * scale[j];
+}
+
+// ---------------------------------------------------------------------------
+// inverse, pass 1: scale + inverse y-pass, CTA = (member k, rhs r)
+//   u[r][k][y][jx] = sum_{j in group(jx)} by[py_j][y] * scale_j * c[r][k][j]
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+inv_ypass(const T* __restrict__ c, const T* __restrict__ by, const int* __restrict__ m_py,
+          const int* __restrict__ grp_start, const int* __restrict__ grp_modes, const T* __restrict__ scale,
+          T* __restrict__ u, int K, int ny, int Px, int L) {
+    extern __shared__ unsigned char smem_raw[];
+    T* cs = reinterpret_cast<T*>(smem_raw);   // [L]
+    const int k = blockIdx.x, r = blockIdx.y;
+    const T* src = c + ((long long)r * K + k) * L;
+    for (int j = threadIdx.x; j < L; j += blockDim.x) cs[j] = src[j] * scale[j];
+    __syncthreads();
+    T* dst = u + ((long long)r * K + k) * ny * Px;
+    for (int e = threadIdx.x; e < ny * Px; e += blockDim.x) {
+        const int yy = e / Px, jx = e - yy * Px;
+        T s = 0;
+        for (int q = grp_start[jx]; q < grp_start[jx + 1]; ++q) {
+            const int j = grp_modes[q];
+            s = fma(by[(size_t)m_py[j] * ny + yy], cs[j], s);
+        }
+        dst[e] = s;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// inverse, pass 2: inverse x-pass + per-column product,
+// CTA = (grid row y, column tile, rhs r); one thread per column
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+inv_xpass_column(const T* __restrict__ u, const T* __restrict__ M, const T* __restrict__ bx, T* __restrict__ out,
+                 int nw, int K, int nx, int ny, int Px) {
+    extern __shared__ unsigned char smem_raw[];
+    T* us = reinterpret_cast<T*>(smem_raw);   // [K][Px]
+    T* ys = us + (size_t)K * Px;              // [K][blockDim]
+    const int y = blockIdx.x;
+    const int xt = blockIdx.y;
+    const int r = blockIdx.z;
+    const long long nh = (long long)nx * ny;
+    for (int e = threadIdx.x; e < K * Px; e += blockDim.x) {
+        const int k = e / Px, jx = e - k * Px;
+        us[e] = u[(((long long)r * K + k) * ny + y) * Px + jx];
+    }
+    __syncthreads();
+    const int xc = xt * blockDim.x + threadIdx.x;
+    if (xc >= nx) return;
+    const long long m = (long long)y * nx + xc;
+    for (int k = 0; k < K; ++k) {
+        T s = 0;
+        for (int jx = 0; jx < Px; ++jx) s = fma(bx[(size_t)jx * nx + xc], us[k * Px + jx], s);
+        ys[(size_t)k * blockDim.x + threadIdx.x] = s;
+    }
+    for (int l = 0; l < nw; ++l) {
+        T s0 = 0, s1 = 0;
+        int k = 0;
+        for (; k + 1 < K; k += 2) {
+            s0 = fma(M[((long long)k * nw + l) * nh + m], ys[(size_t)k * blockDim.x + threadIdx.x], s0);
+            s1 = fma(M[((long long)(k + 1) * nw + l) * nh + m], ys[(size_t)(k + 1) * blockDim.x + threadIdx.x], s1);
+        }
+        if (k < K) s0 = fma(M[((long long)k * nw + l) * nh + m], ys[(size_t)k * blockDim.x + threadIdx.x], s0);
+        out[((long long)r * nw + l) * nh + m] = s0 + s1;
+    }
+}
+
+template <typename T, int RC>
+cudaError_t launch_fwd_rc(const zl_plan_s& p, const T* x, const T* M, const T* bx, T* t1, int R, cudaStream_t s) {
+    const int nx = p.d.nx, ny = p.d.ny, K = p.d.K;
+    const size_t smem = (size_t)KC * RC * nx * sizeof(T);
+    cudaError_t e = cudaFuncSetAttribute(fwd_column_xpass<T, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((K + KC - 1) / KC, (R + RC - 1) / RC, ny);
+    fwd_column_xpass<T, RC><<<grid, kThreads, smem, s>>>(x, M, bx, t1, R, p.d.nw, K, nx, ny, p.Px);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t forward_plain(const zl_plan_s& p, const Tables<T>& t, const T* M, const T* scale, const T* x, T* out,
+                          int R, cudaStream_t s) {
+    const int nx = p.d.nx, ny = p.d.ny, K = p.d.K;
+    T* t1 = reinterpret_cast<T*>(p.t1);
+    cudaError_t e;
+    const size_t row = (size_t)KC * nx * sizeof(T);
+    p.timer.begin(ZL_STAGE_FWD_COLUMN, s);
+    if (R >= 8 && 8 * row <= kRowSmemBudget) e = launch_fwd_rc<T, 8>(p, x, M, t.bx, t1, R, s);
+    else if (R >= 4 && 4 * row <= kRowSmemBudget) e = launch_fwd_rc<T, 4>(p, x, M, t.bx, t1, R, s);
+    else if (R >= 2 && 2 * row <= kRowSmemBudget) e = launch_fwd_rc<T, 2>(p, x, M, t.bx, t1, R, s);
+    else e = launch_fwd_rc<T, 1>(p, x, M, t.bx, t1, R, s);
+    p.timer.end(s);
+    if (e != cudaSuccess) return e;
+
+    int ychunk = ny;
+    while ((size_t)(p.L + p.Px * ychunk) * sizeof(T) > 96 * 1024 && ychunk > 1) ychunk = (ychunk + 1) / 2;
+    const size_t smem = (size_t)(p.L + p.Px * ychunk) * sizeof(T);
+    e = cudaFuncSetAttribute(fwd_ypass<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    p.timer.begin(ZL_STAGE_FWD_YPASS, s);
+    fwd_ypass<T><<<dim3(K, R), kThreads, smem, s>>>(t1, t.by, t.m_py, t.m_jx, scale, out, K, ny, p.Px, p.L, ychunk);
+    p.timer.end(s);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t inverse_plain(const zl_plan_s& p, const Tables<T>& t, const T* M, const T* scale, const T* c, T* out,
+                          int R, cudaStream_t s) {
+    const int nx = p.d.nx, ny = p.d.ny, K = p.d.K;
+    T* u = reinterpret_cast<T*>(p.t1);
+    size_t smem = (size_t)p.L * sizeof(T);
+    cudaError_t e = cudaFuncSetAttribute(inv_ypass<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    p.timer.begin(ZL_STAGE_INV_YPASS, s);
+    inv_ypass<T><<<dim3(K, R), kThreads, smem, s>>>(c, t.by, t.m_py, t.grp_start, t.grp_modes, scale, u, K, ny, p.Px, p.L);
+    p.timer.end(s);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    int threads = nx < kThreads ? ((nx + 31) / 32) * 32 : kThreads;
+    while ((size_t)K * (p.Px + threads) * sizeof(T) > 160 * 1024 && threads > 32) threads /= 2;
+    smem = (size_t)K * (p.Px + threads) * sizeof(T);
+    e = cudaFuncSetAttribute(inv_xpass_column<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid(ny, (nx + threads - 1) / threads, R);
+    p.timer.begin(ZL_STAGE_INV_COLUMN, s);
+    inv_xpass_column<T><<<grid, threads, smem, s>>>(u, M, t.bx, out, p.d.nw, K, nx, ny, p.Px);
+    p.timer.end(s);
+    return cudaGetLastError();
+}
+
+template cudaError_t forward_plain<double>(const zl_plan_s&, const Tables<double>&, const double*, const double*,
+                                           const double*, double*, int, cudaStream_t);
+template cudaError_t forward_plain<float>(const zl_plan_s&, const Tables<float>&, const float*, const float*,
+                                          const float*, float*, int, cudaStream_t);
+template cudaError_t inverse_plain<double>(const zl_plan_s&, const Tables<double>&, const double*, const double*,
+                                           const double*, double*, int, cudaStream_t);
+template cudaError_t inverse_plain<float>(const zl_plan_s&, const Tables<float>&, const float*, const float*,
+                                          const float*, float*, int, cudaStream_t);
+
+}  // namespace zl

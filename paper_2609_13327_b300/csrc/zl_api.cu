@@ -1,0 +1,426 @@
+// libzl C ABI: plan lifecycle, argument checking, host-side tables, dispatch.
+
+#include "zl_internal.cuh"
+
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <numeric>
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// packed real-Fourier basis (one axis of length N)
+// ---------------------------------------------------------------------------
+int packed_frequency(int N, int p) {
+    if (p == 0) return 0;
+    if (N % 2 == 0 && p == N - 1) return N / 2;
+    return (p + 1) / 2;
+}
+
+// b_p(m); the argument 2 pi j m / N is reduced exactly in integers first.
+double basis_value(int N, int p, int m) {
+    if (p == 0) return 1.0 / std::sqrt((double)N);
+    if (N % 2 == 0 && p == N - 1) return ((m & 1) ? -1.0 : 1.0) / std::sqrt((double)N);
+    const int j = (p + 1) / 2;
+    const long long r = ((long long)j * m) % N;
+    const double a = 2.0 * M_PI * (double)r / (double)N;
+    return std::sqrt(2.0 / N) * ((p & 1) ? std::cos(a) : std::sin(a));
+}
+
+std::vector<double> gaussian_axis_spectrum(int N, double ell) {
+    std::vector<double> lam(N, 1.0);
+    if (N == 1) return lam;
+    const int P = (int)std::ceil(12.0 * ell / N) + 2;
+    std::vector<double> c(N, 0.0);
+    double den = 0.0;
+    for (int p = -P; p <= P; ++p) {
+        const double t = (double)p * N;
+        den += std::exp(-t * t / (2.0 * ell * ell));
+        for (int d = 0; d < N; ++d) {
+            const double u = d + t;
+            c[d] += std::exp(-u * u / (2.0 * ell * ell));
+        }
+    }
+    for (int d = 0; d < N; ++d) c[d] /= den;
+    for (int p = 0; p < N; ++p) {
+        const int f = packed_frequency(N, p);
+        double s = 0.0;
+        for (int d = 0; d < N; ++d) s += c[d] * std::cos(2.0 * M_PI * (double)(((long long)f * d) % N) / N);
+        lam[p] = s;
+    }
+    return lam;
+}
+
+template <typename T>
+cudaError_t upload(T** dst, const std::vector<T>& src, cudaStream_t s) {
+    cudaError_t e = cudaMalloc((void**)dst, std::max<size_t>(1, src.size()) * sizeof(T));
+    if (e != cudaSuccess) return e;
+    if (src.empty()) return cudaSuccess;
+    e = cudaMemcpyAsync(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    return cudaStreamSynchronize(s);   // src is a temporary host vector
+}
+
+template <typename T>
+cudaError_t build_tables(zl_plan_s& p, zl::Tables<T>& t, const std::vector<double>& lamS,
+                         const std::vector<int>& xfreq, cudaStream_t s) {
+    const int nx = p.d.nx, ny = p.d.ny, L = p.L, Px = p.Px;
+    std::vector<T> bx((size_t)Px * nx), by((size_t)ny * ny), isl(L), sl(L);
+    for (int jx = 0; jx < Px; ++jx)
+        for (int x = 0; x < nx; ++x) bx[(size_t)jx * nx + x] = (T)basis_value(nx, xfreq[jx], x);
+    for (int q = 0; q < ny; ++q)
+        for (int y = 0; y < ny; ++y) by[(size_t)q * ny + y] = (T)basis_value(ny, q, y);
+    std::vector<int> py(L), jxv(L);
+    std::vector<int> xslot(nx, -1);
+    for (int jx = 0; jx < Px; ++jx) xslot[xfreq[jx]] = jx;
+    for (int j = 0; j < L; ++j) {
+        py[j] = p.modes[j] / nx;
+        jxv[j] = xslot[p.modes[j] % nx];
+        isl[j] = (T)(1.0 / std::sqrt(lamS[j]));
+        sl[j] = (T)std::sqrt(lamS[j]);
+    }
+    std::vector<int> gstart(Px + 1, 0), gmodes(L);
+    for (int j = 0; j < L; ++j) gstart[jxv[j] + 1]++;
+    for (int q = 0; q < Px; ++q) gstart[q + 1] += gstart[q];
+    std::vector<int> fill(gstart.begin(), gstart.end() - 1);
+    for (int j = 0; j < L; ++j) gmodes[fill[jxv[j]]++] = j;
+    cudaError_t e;
+    if ((e = upload(&t.bx, bx, s)) != cudaSuccess) return e;
+    if ((e = upload(&t.by, by, s)) != cudaSuccess) return e;
+    if ((e = upload(&t.inv_sqrt_lam, isl, s)) != cudaSuccess) return e;
+    if ((e = upload(&t.sqrt_lam, sl, s)) != cudaSuccess) return e;
+    if ((e = upload(&t.m_py, py, s)) != cudaSuccess) return e;
+    if ((e = upload(&t.m_jx, jxv, s)) != cudaSuccess) return e;
+    if ((e = upload(&t.grp_start, gstart, s)) != cudaSuccess) return e;
+    return upload(&t.grp_modes, gmodes, s);
+}
+
+template <typename T>
+void free_tables(zl::Tables<T>& t) {
+    cudaFree(t.bx);
+    cudaFree(t.by);
+    cudaFree(t.inv_sqrt_lam);
+    cudaFree(t.sqrt_lam);
+    cudaFree(t.m_py);
+    cudaFree(t.m_jx);
+    cudaFree(t.grp_start);
+    cudaFree(t.grp_modes);
+    t = zl::Tables<T>();
+}
+
+void free_plan(zl_plan_s* p) {
+    if (!p) return;
+    zl::tc_release(*p);
+    cudaFree(p->Zc);
+    cudaFree(p->P);
+    cudaFree(p->t1);
+    cudaFree(p->h_x);
+    cudaFree(p->h_xt);
+    cudaFree(p->d_status);
+    free_tables(p->td);
+    free_tables(p->tf);
+    delete p;
+}
+
+zl_status cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return ZL_OK;
+    if (e == cudaErrorMemoryAllocation) return ZL_ERR_ALLOC;
+    return ZL_ERR_CUDA;
+}
+
+bool valid_plan(zl_plan p) { return p != nullptr && p->P != nullptr; }
+
+// Operator kinds for the shared forward / inverse passes.
+enum class Op { LeftInverse, SqrtAdjoint, Sqrt, Adjoint };
+
+zl_status run(zl_plan p, Op op, const void* in, void* out, int R, void* stream) {
+    if (!valid_plan(p) || (R > 0 && (in == nullptr || out == nullptr)) || R < 0) return ZL_ERR_ARG;
+    if (p->bad_column >= 0) return ZL_ERR_RANK;
+    if (R == 0) return ZL_OK;
+    if (in == out) return ZL_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long n = (long long)p->d.nw * p->nh;
+    const long long ns = (long long)p->d.K * p->L;
+    const bool fwd = (op == Op::LeftInverse || op == Op::SqrtAdjoint);
+    const long long in_len = fwd ? n : ns, out_len = fwd ? ns : n;
+    const int chunk = p->d.max_rhs;
+    for (int r0 = 0; r0 < R; r0 += chunk) {
+        const int rc = std::min(chunk, R - r0);
+        cudaError_t e;
+        if (p->d.prec == ZL_FP64) {
+            const double* x = (const double*)in + (long long)r0 * in_len;
+            double* o = (double*)out + (long long)r0 * out_len;
+            const double* M = (const double*)((op == Op::LeftInverse || op == Op::Adjoint) ? p->P : p->Zc);
+            const double* sc = (op == Op::LeftInverse || op == Op::Adjoint) ? p->td.inv_sqrt_lam : p->td.sqrt_lam;
+            e = fwd ? zl::forward_plain<double>(*p, p->td, M, sc, x, o, rc, s)
+                    : zl::inverse_plain<double>(*p, p->td, M, sc, x, o, rc, s);
+        } else {
+            const float* x = (const float*)in + (long long)r0 * in_len;
+            float* o = (float*)out + (long long)r0 * out_len;
+            if (op == Op::LeftInverse && p->d.prec == ZL_MIXED && p->tc != nullptr) {
+                e = zl::forward_tc(*p, x, o, rc, s);
+            } else {
+                const float* M = (const float*)((op == Op::LeftInverse || op == Op::Adjoint) ? p->P : p->Zc);
+                const float* sc = (op == Op::LeftInverse || op == Op::Adjoint) ? p->tf.inv_sqrt_lam : p->tf.sqrt_lam;
+                e = fwd ? zl::forward_plain<float>(*p, p->tf, M, sc, x, o, rc, s)
+                        : zl::inverse_plain<float>(*p, p->tf, M, sc, x, o, rc, s);
+            }
+        }
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    return ZL_OK;
+}
+
+}  // namespace
+
+namespace zl {
+
+cudaEvent_t StageTimer::take() {
+    if (!pool.empty()) {
+        cudaEvent_t e = pool.back();
+        pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+void StageTimer::begin(int stage, cudaStream_t s) {
+    if (!on) return;
+    Rec r{stage, take(), take()};
+    if (r.a == nullptr || r.b == nullptr) return;
+    cudaEventRecord(r.a, s);
+    recs.push_back(r);
+}
+
+void StageTimer::end(cudaStream_t s) {
+    if (!on || recs.empty()) return;
+    cudaEventRecord(recs.back().b, s);
+}
+
+void StageTimer::clear() {
+    for (auto& r : recs) {
+        cudaEventSynchronize(r.b);
+        pool.push_back(r.a);
+        pool.push_back(r.b);
+    }
+    recs.clear();
+}
+
+StageTimer::~StageTimer() {
+    clear();
+    for (cudaEvent_t e : pool) cudaEventDestroy(e);
+}
+
+}  // namespace zl
+
+extern "C" {
+
+zl_status zl_set_stage_timing(zl_plan p, int enable) {
+    if (!valid_plan(p)) return ZL_ERR_ARG;
+    if (enable) p->timer.clear();
+    p->timer.on = enable != 0;
+    return ZL_OK;
+}
+
+zl_status zl_get_stage_times(zl_plan p, int stage, int* launches, double* total_ms) {
+    if (!valid_plan(p) || stage < 0 || stage >= ZL_NUM_STAGES || launches == nullptr || total_ms == nullptr)
+        return ZL_ERR_ARG;
+    int n = 0;
+    double ms = 0.0;
+    for (auto& r : p->timer.recs) {
+        if (r.stage != stage) continue;
+        if (cudaEventSynchronize(r.b) != cudaSuccess) return ZL_ERR_CUDA;
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, r.a, r.b) != cudaSuccess) return ZL_ERR_CUDA;
+        ms += t;
+        ++n;
+    }
+    *launches = n;
+    *total_ms = ms;
+    return ZL_OK;
+}
+
+
+const char* zl_status_string(zl_status s) {
+    switch (s) {
+        case ZL_OK: return "ZL_OK";
+        case ZL_ERR_ARG: return "ZL_ERR_ARG: invalid argument";
+        case ZL_ERR_SHAPE: return "ZL_ERR_SHAPE: size outside the supported range";
+        case ZL_ERR_RANK: return "ZL_ERR_RANK: a column matrix A_m is rank-deficient";
+        case ZL_ERR_ALLOC: return "ZL_ERR_ALLOC: device allocation failed";
+        case ZL_ERR_CUDA: return "ZL_ERR_CUDA: CUDA runtime error";
+        case ZL_ERR_TIMEOUT: return "ZL_ERR_TIMEOUT: a bounded device wait gave up";
+        case ZL_ERR_UNSUPPORTED: return "ZL_ERR_UNSUPPORTED: not implemented for this configuration";
+    }
+    return "unknown zl_status";
+}
+
+zl_status zl_gaussian_spectrum(int nx, int ny, double ell, double* out) {
+    if (out == nullptr || !(ell > 0.0) || !std::isfinite(ell)) return ZL_ERR_ARG;
+    if (nx < 1 || ny < 1 || (long long)nx * ny > (1LL << 30)) return ZL_ERR_SHAPE;
+    const std::vector<double> lx = gaussian_axis_spectrum(nx, ell), ly = gaussian_axis_spectrum(ny, ell);
+    for (int q = 0; q < ny; ++q)
+        for (int p = 0; p < nx; ++p) out[(size_t)q * nx + p] = ly[q] * lx[p];
+    return ZL_OK;
+}
+
+zl_status zl_setup(const zl_desc* desc, const void* Z, const double* spectrum, void* stream, zl_plan* out) {
+    if (out == nullptr) return ZL_ERR_ARG;
+    *out = nullptr;
+    if (desc == nullptr || Z == nullptr || spectrum == nullptr) return ZL_ERR_ARG;
+    const zl_desc d = *desc;
+    if (d.prec != ZL_FP64 && d.prec != ZL_FP32 && d.prec != ZL_MIXED) return ZL_ERR_ARG;
+    if (!(d.tau >= 0.0) || !std::isfinite(d.tau)) return ZL_ERR_ARG;
+    if (d.nx < 1 || d.ny < 1 || d.nw < 1 || d.K < 1 || d.max_rhs < 1 || d.max_rhs > 65535) return ZL_ERR_SHAPE;
+    if (d.nx > 65535 || d.ny > 65535) return ZL_ERR_SHAPE;
+    const long long nh = (long long)d.nx * d.ny;
+    if (nh > (1LL << 30) || (long long)d.nw * d.K > 16384) return ZL_ERR_SHAPE;
+    if (zl::setup_smem_bytes(d.nw, d.K) > 200 * 1024) return ZL_ERR_SHAPE;
+    double lmax = -INFINITY;
+    for (long long s = 0; s < nh; ++s) {
+        if (!std::isfinite(spectrum[s])) return ZL_ERR_ARG;
+        lmax = std::max(lmax, spectrum[s]);
+    }
+    if (!(lmax > 0.0)) return ZL_ERR_ARG;
+
+    zl_plan_s* p = new (std::nothrow) zl_plan_s();
+    if (!p) return ZL_ERR_ALLOC;
+    p->d = d;
+    p->nh = nh;
+    p->g = std::min(d.nw, d.K);
+    p->esize = d.prec == ZL_FP64 ? sizeof(double) : sizeof(float);
+    std::vector<double> lamS;
+    for (long long s = 0; s < nh; ++s)
+        if (spectrum[s] > d.tau * lmax) {
+            p->modes.push_back((int)s);
+            lamS.push_back(spectrum[s]);
+        }
+    p->L = (int)p->modes.size();
+    std::vector<char> used(d.nx, 0);
+    for (int s : p->modes) used[s % d.nx] = 1;
+    std::vector<int> xfreq;
+    for (int q = 0; q < d.nx; ++q)
+        if (used[q]) xfreq.push_back(q);
+    p->Px = (int)xfreq.size();
+    // forward y-pass keeps the L accumulators in shared memory
+    if ((size_t)p->L * p->esize + (size_t)p->Px * p->esize > 96 * 1024 ||
+        (size_t)d.K * (p->Px + 32) * p->esize > 160 * 1024) {
+        delete p;
+        return ZL_ERR_SHAPE;
+    }
+
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t mbytes = (size_t)d.K * d.nw * nh * p->esize;
+    const size_t tbytes = (size_t)d.max_rhs * d.K * d.ny * p->Px * p->esize;
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = cudaMalloc(&p->Zc, mbytes);
+    if (e == cudaSuccess) e = cudaMalloc(&p->P, mbytes);
+    if (e == cudaSuccess) e = cudaMalloc(&p->t1, std::max<size_t>(tbytes, 16));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&p->d_status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p->Zc, Z, mbytes, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) {
+        static const int kNone = INT_MAX;
+        e = cudaMemcpyAsync(p->d_status, &kNone, sizeof(int), cudaMemcpyHostToDevice, s);
+    }
+    if (e == cudaSuccess) {
+        e = d.prec == ZL_FP64 ? build_tables<double>(*p, p->td, lamS, xfreq, s)
+                              : build_tables<float>(*p, p->tf, lamS, xfreq, s);
+    }
+    if (e == cudaSuccess) e = zl::launch_setup_columns(d, nh, Z, p->P, p->d_status, s);
+    int status = INT_MAX;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&status, p->d_status, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        free_plan(p);
+        return cuda_status(e);
+    }
+    if (status != INT_MAX) {
+        p->bad_column = status;
+        *out = p;
+        return ZL_ERR_RANK;
+    }
+    if (d.prec == ZL_MIXED) {
+        const zl_status ts = zl::tc_prepare(*p, s);
+        if (ts != ZL_OK && ts != ZL_ERR_UNSUPPORTED) {
+            free_plan(p);
+            return ts;
+        }
+    }
+    *out = p;
+    return ZL_OK;
+}
+
+zl_status zl_get_info(zl_plan p, int* L, int* nw, int* K, long long* nh, int* bad_column) {
+    if (!valid_plan(p)) return ZL_ERR_ARG;
+    if (L) *L = p->L;
+    if (nw) *nw = p->d.nw;
+    if (K) *K = p->d.K;
+    if (nh) *nh = p->nh;
+    if (bad_column) *bad_column = p->bad_column;
+    return ZL_OK;
+}
+
+zl_status zl_get_modes(zl_plan p, int* modes) {
+    if (!valid_plan(p) || modes == nullptr) return ZL_ERR_ARG;
+    std::copy(p->modes.begin(), p->modes.end(), modes);
+    return ZL_OK;
+}
+
+zl_status zl_apply_left_inverse(zl_plan p, const void* x, void* xt, int R, void* stream) {
+    return run(p, Op::LeftInverse, x, xt, R, stream);
+}
+
+zl_status zl_apply_sqrt_adjoint(zl_plan p, const void* x, void* t, int R, void* stream) {
+    return run(p, Op::SqrtAdjoint, x, t, R, stream);
+}
+
+zl_status zl_apply_sqrt(zl_plan p, const void* xt, void* x, int R, void* stream) {
+    return run(p, Op::Sqrt, xt, x, R, stream);
+}
+
+zl_status zl_apply_adjoint(zl_plan p, const void* y, void* g, int R, void* stream) {
+    return run(p, Op::Adjoint, y, g, R, stream);
+}
+
+zl_status zl_apply_left_inverse_host(zl_plan p, const void* x, void* xt, int R, void* stream) {
+    if (!valid_plan(p) || R < 0 || (R > 0 && (x == nullptr || xt == nullptr))) return ZL_ERR_ARG;
+    if (p->bad_column >= 0) return ZL_ERR_RANK;
+    if (R == 0) return ZL_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t in_b = (size_t)p->d.nw * p->nh * p->esize, out_b = (size_t)p->d.K * p->L * p->esize;
+    const int chunk = p->d.max_rhs;
+    cudaError_t e = cudaSuccess;
+    if (p->h_x == nullptr) {
+        e = cudaMalloc(&p->h_x, in_b * chunk);
+        if (e == cudaSuccess) e = cudaMalloc(&p->h_xt, out_b * chunk);
+        if (e != cudaSuccess) {
+            cudaFree(p->h_x);
+            p->h_x = p->h_xt = nullptr;
+            return cuda_status(e);
+        }
+    }
+    for (int r0 = 0; r0 < R; r0 += chunk) {
+        const int rc = std::min(chunk, R - r0);
+        e = cudaMemcpyAsync(p->h_x, (const char*)x + r0 * in_b, rc * in_b, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return cuda_status(e);
+        const zl_status st = run(p, Op::LeftInverse, p->h_x, p->h_xt, rc, stream);
+        if (st != ZL_OK) return st;
+        e = cudaMemcpyAsync((char*)xt + r0 * out_b, p->h_xt, rc * out_b, cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    return cuda_status(cudaStreamSynchronize(s));
+}
+
+zl_status zl_destroy(zl_plan p) {
+    if (p == nullptr) return ZL_OK;
+    free_plan(p);
+    return ZL_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,98 @@
+// Internal declarations shared by the libzl translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <vector>
+
+#include "../../include/zl.h"
+
+namespace zl {
+
+// Device-resident tables of the horizontal transform, in the plan's element type T.
+//   bx      [Px][nx]   b_{p_x}(x) for the kept x-frequencies, in kept order
+//   by      [ny][ny]   b_{p_y}(y), row p_y
+//   m_py    [L]        packed y-index of output mode j
+//   m_jx    [L]        index into the kept x-frequency list of output mode j
+//   inv_sqrt_lam, sqrt_lam [L]
+//   grp_start [Px+1], grp_modes [L]: output modes grouped by jx (for the inverse y-pass)
+template <typename T>
+struct Tables {
+    T* bx = nullptr;
+    T* by = nullptr;
+    T* inv_sqrt_lam = nullptr;
+    T* sqrt_lam = nullptr;
+    int* m_py = nullptr;
+    int* m_jx = nullptr;
+    int* grp_start = nullptr;
+    int* grp_modes = nullptr;
+};
+
+struct TcOperands;   // tensor-core path state (k_tc.cu)
+
+// Optional CUDA-event bracketing of every kernel stage (zl_set_stage_timing).
+struct StageTimer {
+    struct Rec {
+        int stage;
+        cudaEvent_t a, b;
+    };
+    bool on = false;
+    std::vector<Rec> recs;
+    std::vector<cudaEvent_t> pool;   // events of cleared records, reused
+    cudaEvent_t take();
+    void begin(int stage, cudaStream_t s);
+    void end(cudaStream_t s);
+    void clear();
+    ~StageTimer();
+};
+
+}  // namespace zl
+
+struct zl_plan_s {
+    zl_desc d;
+    long long nh = 0;
+    int g = 0;              // min(nw, K)
+    int L = 0;              // kept modes
+    int Px = 0;             // kept x-frequencies
+    int bad_column = -1;
+    std::vector<int> modes; // kept packed indices (host copy)
+    size_t esize = 0;       // element size of caller buffers (8 or 4)
+
+    // member matrices, [K][nw][nh]: the plan's copy of Z and the pseudo-inverse P (P[k][l][m] = (A_m^+)[k][l])
+    void* Zc = nullptr;
+    void* P = nullptr;
+    // intermediate of the separable transform, [max_rhs][K][ny][Px]
+    void* t1 = nullptr;
+    zl::Tables<double> td;
+    zl::Tables<float> tf;
+    zl::TcOperands* tc = nullptr;
+    // staging for zl_apply_left_inverse_host (allocated on first use)
+    void* h_x = nullptr;
+    void* h_xt = nullptr;
+    int* d_status = nullptr;
+    mutable zl::StageTimer timer;
+};
+
+namespace zl {
+
+// k_setup.cu
+cudaError_t launch_setup_columns(const zl_desc& d, long long nh, const void* Z, void* P, int* d_status,
+                                 cudaStream_t s);
+size_t setup_smem_bytes(int nw, int K);
+
+// k_plain.cu: forward (V1-V5 shape) and inverse (V_b, then per-column product) passes
+//   forward:  out[r][k][j] = scale[j] * sum_m V_b[m][s_j] * sum_l M[k][l][m] x[r][l][m]
+//   inverse:  out[r][l][m] = sum_k M[k][l][m] * sum_j V_b[m][s_j] scale[j] c[r][k][j]
+template <typename T>
+cudaError_t forward_plain(const zl_plan_s& p, const Tables<T>& t, const T* M, const T* scale, const T* x, T* out,
+                          int R, cudaStream_t s);
+template <typename T>
+cudaError_t inverse_plain(const zl_plan_s& p, const Tables<T>& t, const T* M, const T* scale, const T* c, T* out,
+                          int R, cudaStream_t s);
+
+// k_tc.cu: tensor-core left inverse (ZL_MIXED)
+zl_status tc_prepare(zl_plan_s& p, cudaStream_t s);
+void tc_release(zl_plan_s& p);
+cudaError_t forward_tc(const zl_plan_s& p, const float* x, float* out, int R, cudaStream_t s);
+
+}  // namespace zl

@@ -1,0 +1,218 @@
+"""Thin Python binding of libzl (ctypes).  Argument marshalling only.
+
+Every computation runs in libzl's CUDA kernels; this module checks tensor
+dtypes, devices, shapes and contiguity, passes raw device pointers and the
+current CUDA stream, and turns status codes into exceptions.  PyTorch is used
+only for device memory and streams.  If ``libzl.so`` has not been built the
+import of this module fails loudly: there is no CPU fallback.
+"""
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIBPATH = os.path.join(_HERE, "libzl.so")
+
+if not os.path.exists(LIBPATH):
+    raise ImportError(f"libzl.so is not built ({LIBPATH}); run `python -m paper_2609_13327_b300.build`")
+
+_lib = ctypes.CDLL(LIBPATH)
+
+ZL_OK, ZL_ERR_ARG, ZL_ERR_SHAPE, ZL_ERR_RANK, ZL_ERR_ALLOC, ZL_ERR_CUDA, ZL_ERR_TIMEOUT, ZL_ERR_UNSUPPORTED = range(8)
+ZL_FP64, ZL_FP32, ZL_MIXED = 0, 1, 2
+PRECISIONS = {"fp64": ZL_FP64, "fp32": ZL_FP32, "mixed": ZL_MIXED}
+
+# every symbol declared in include/zl.h
+EXPORTS = ["zl_setup", "zl_get_info", "zl_get_modes", "zl_apply_left_inverse", "zl_apply_left_inverse_host",
+           "zl_apply_sqrt", "zl_apply_adjoint", "zl_apply_sqrt_adjoint", "zl_destroy", "zl_status_string",
+           "zl_gaussian_spectrum", "zl_set_stage_timing", "zl_get_stage_times"]
+STAGES = {"fwd_column": 0, "fwd_ypass": 1, "inv_ypass": 2, "inv_column": 3}
+
+
+class zl_desc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nw", ctypes.c_int), ("K", ctypes.c_int),
+                ("prec", ctypes.c_int), ("tau", ctypes.c_double), ("max_rhs", ctypes.c_int)]
+
+
+_vp, _int, _ip, _llp, _dp = ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int), \
+    ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double)
+_lib.zl_setup.argtypes = [ctypes.POINTER(zl_desc), _vp, _dp, _vp, ctypes.POINTER(_vp)]
+_lib.zl_get_info.argtypes = [_vp, _ip, _ip, _ip, _llp, _ip]
+_lib.zl_get_modes.argtypes = [_vp, _ip]
+for _name in ("zl_apply_left_inverse", "zl_apply_left_inverse_host", "zl_apply_sqrt", "zl_apply_adjoint",
+              "zl_apply_sqrt_adjoint"):
+    getattr(_lib, _name).argtypes = [_vp, _vp, _vp, _int, _vp]
+_lib.zl_destroy.argtypes = [_vp]
+_lib.zl_status_string.argtypes = [_int]
+_lib.zl_status_string.restype = ctypes.c_char_p
+_lib.zl_gaussian_spectrum.argtypes = [_int, _int, ctypes.c_double, _dp]
+_lib.zl_set_stage_timing.argtypes = [_vp, _int]
+_lib.zl_get_stage_times.argtypes = [_vp, _int, _ip, _dp]
+for _name in EXPORTS:
+    if _name != "zl_status_string":
+        getattr(_lib, _name).restype = _int
+
+
+class ZLError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__(f"{where}: {zl_status_string(code)}")
+
+
+def zl_status_string(code):
+    return _lib.zl_status_string(int(code)).decode()
+
+
+def _check(code, where):
+    if code != ZL_OK:
+        raise ZLError(code, where)
+
+
+def zl_gaussian_spectrum(nx, ny, ell):
+    """Eigenvalues of the separable periodized-Gaussian localization, packed order (host, float64)."""
+    out = np.empty(nx * ny, dtype=np.float64)
+    _check(_lib.zl_gaussian_spectrum(nx, ny, float(ell), out.ctypes.data_as(_dp)), "zl_gaussian_spectrum")
+    return out
+
+
+def _stream_handle(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Plan:
+    """Owns a zl_plan handle; freed by ``destroy()`` or garbage collection."""
+
+    def __init__(self, handle, desc):
+        self.handle = handle
+        self.desc = desc
+        L, nw, K, nh, bad = _int(), _int(), _int(), ctypes.c_longlong(), _int()
+        _check(_lib.zl_get_info(handle, ctypes.byref(L), ctypes.byref(nw), ctypes.byref(K), ctypes.byref(nh),
+                                ctypes.byref(bad)), "zl_get_info")
+        self.L, self.nw, self.K, self.nh, self.bad_column = L.value, nw.value, K.value, nh.value, bad.value
+        self.prec = desc.prec
+        self.nx, self.ny = desc.nx, desc.ny
+
+    @property
+    def dtype(self):
+        import torch
+        return torch.float64 if self.prec == ZL_FP64 else torch.float32
+
+    def modes(self):
+        out = np.empty(self.L, dtype=np.int32)
+        _check(_lib.zl_get_modes(self.handle, out.ctypes.data_as(_ip)), "zl_get_modes")
+        return out
+
+    def set_stage_timing(self, enable):
+        _check(_lib.zl_set_stage_timing(self.handle, 1 if enable else 0), "zl_set_stage_timing")
+
+    def stage_times(self):
+        """{stage name: (launches, total ms)} of the recorded stage launches."""
+        out = {}
+        for name, sid in STAGES.items():
+            n, ms = _int(), ctypes.c_double()
+            _check(_lib.zl_get_stage_times(self.handle, sid, ctypes.byref(n), ctypes.byref(ms)), "zl_get_stage_times")
+            out[name] = (n.value, ms.value)
+        return out
+
+    def destroy(self):
+        if self.handle:
+            _lib.zl_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def zl_setup(Z, spectrum, tau=1e-10, prec="fp32", max_rhs=64, stream=None, nx=None, ny=None):
+    """Build a plan from a device ensemble Z [K][n_w][n_h] and a host spectrum [n_h].
+
+    ``nx``/``ny`` give the grid (default: a ring, ny = 1).  Raises ZLError; on a
+    rank-deficient ensemble the error carries ``code == ZL_ERR_RANK`` and the
+    offending column is available as ``err.bad_column``.
+    """
+    import torch
+    p = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
+    want = torch.float64 if p == ZL_FP64 else torch.float32
+    if not (isinstance(Z, torch.Tensor) and Z.is_cuda and Z.dtype == want and Z.dim() == 3 and Z.is_contiguous()):
+        raise ValueError(f"Z must be a contiguous CUDA {want} tensor [K][n_w][n_h]")
+    K, nw, nh = Z.shape
+    if nx is None:
+        nx, ny = nh, 1
+    if nx * ny != nh:
+        raise ValueError("nx * ny must equal Z.shape[2]")
+    spec = np.ascontiguousarray(spectrum, dtype=np.float64)
+    if spec.shape != (nh,):
+        raise ValueError("spectrum must have n_h entries")
+    d = zl_desc(nx, ny, nw, K, p, float(tau), int(max_rhs))
+    h = _vp()
+    code = _lib.zl_setup(ctypes.byref(d), _vp(Z.data_ptr()), spec.ctypes.data_as(_dp), _stream_handle(stream),
+                         ctypes.byref(h))
+    if code == ZL_ERR_RANK:
+        plan = Plan(h, d)
+        err = ZLError(code, "zl_setup")
+        err.bad_column = plan.bad_column
+        plan.destroy()
+        raise err
+    _check(code, "zl_setup")
+    return Plan(h, d)
+
+
+def _apply(fn, plan, inp, in_shape, out_shape, out, stream, where):
+    import torch
+    if not (isinstance(inp, torch.Tensor) and inp.is_cuda and inp.dtype == plan.dtype and inp.is_contiguous()):
+        raise ValueError(f"{where}: input must be a contiguous CUDA {plan.dtype} tensor")
+    if inp.dim() != 3 or tuple(inp.shape[1:]) != in_shape:
+        raise ValueError(f"{where}: input shape must be [R]{list(in_shape)}")
+    R = inp.shape[0]
+    if out is None:
+        out = torch.empty((R,) + out_shape, dtype=plan.dtype, device=inp.device)
+    elif not (out.is_cuda and out.dtype == plan.dtype and out.is_contiguous() and tuple(out.shape) == (R,) + out_shape):
+        raise ValueError(f"{where}: bad output tensor")
+    _check(fn(plan.handle, _vp(inp.data_ptr()), _vp(out.data_ptr()), R, _stream_handle(stream)), where)
+    return out
+
+
+def zl_apply_left_inverse(plan, x, out=None, stream=None):
+    """x~ = Zh^- x: x [R][n_w][n_h] -> x~ [R][K][L]."""
+    return _apply(_lib.zl_apply_left_inverse, plan, x, (plan.nw, plan.nh), (plan.K, plan.L), out, stream,
+                  "zl_apply_left_inverse")
+
+
+def zl_apply_sqrt_adjoint(plan, x, out=None, stream=None):
+    """Zh^T x: x [R][n_w][n_h] -> [R][K][L]."""
+    return _apply(_lib.zl_apply_sqrt_adjoint, plan, x, (plan.nw, plan.nh), (plan.K, plan.L), out, stream,
+                  "zl_apply_sqrt_adjoint")
+
+
+def zl_apply_sqrt(plan, xt, out=None, stream=None):
+    """x = Zh x~: x~ [R][K][L] -> x [R][n_w][n_h]."""
+    return _apply(_lib.zl_apply_sqrt, plan, xt, (plan.K, plan.L), (plan.nw, plan.nh), out, stream, "zl_apply_sqrt")
+
+
+def zl_apply_adjoint(plan, y, out=None, stream=None):
+    """g = (Zh^-)^T y: y [R][K][L] -> g [R][n_w][n_h]."""
+    return _apply(_lib.zl_apply_adjoint, plan, y, (plan.K, plan.L), (plan.nw, plan.nh), out, stream,
+                  "zl_apply_adjoint")
+
+
+def zl_apply_left_inverse_host(plan, x, out=None, stream=None):
+    """Host-buffer variant: x and out are CPU tensors (pinned for asynchronous copies)."""
+    import torch
+    if not (isinstance(x, torch.Tensor) and not x.is_cuda and x.dtype == plan.dtype and x.is_contiguous()):
+        raise ValueError("zl_apply_left_inverse_host: x must be a contiguous CPU tensor")
+    if x.dim() != 3 or tuple(x.shape[1:]) != (plan.nw, plan.nh):
+        raise ValueError("zl_apply_left_inverse_host: bad input shape")
+    R = x.shape[0]
+    if out is None:
+        out = torch.empty((R, plan.K, plan.L), dtype=plan.dtype, pin_memory=x.is_pinned())
+    _check(_lib.zl_apply_left_inverse_host(plan.handle, _vp(x.data_ptr()), _vp(out.data_ptr()), R,
+                                           _stream_handle(stream)), "zl_apply_left_inverse_host")
+    return out
