@@ -292,7 +292,7 @@ def run_ours(args, w, prec):
     bpr = algorithmic_bytes_per_rhs(w, plan.L, prec, R)
     peak, peak_kind = measured_peak_hbm()
     achieved = bpr * R / avg_col_s / 1e9
-    kernel_name = "zl_fwd_column_tc" if (prec == "mixed" and plan_uses_tc(plan)) else "fwd_column_xpass"
+    kernel_name = "fwd_column_tc_kernel" if (prec == "mixed" and plan_uses_tc(plan)) else "fwd_column_xpass"
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": recorded_traffic(kernel_name, w.name, prec), "kernel": kernel_name,
                 "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback",

@@ -114,6 +114,19 @@ zl_status zl_setup(const zl_desc* desc, const void* Z, const double* spectrum,
 zl_status zl_get_info(zl_plan plan, int* L, int* nw, int* K, long long* nh, int* bad_column);
 
 /*
+ * zl_get_runtime_info -- which kernel path the plan's left inverse takes and
+ * whether a device-side wait has given up.  Either pointer may be NULL.
+ *   tensor_core_path  1 if zl_apply_left_inverse runs the tcgen05 kernel
+ *                     (ZL_MIXED plans whose shape it supports: nx a multiple of
+ *                     16 and <= 256, nw <= 32, K <= 64, at most 48 kept
+ *                     x-frequencies), 0 if it runs the CUDA-core kernels.
+ *   device_error      0, or the code the tensor-core kernel recorded when one
+ *                     of its bounded waits timed out (the call then returns
+ *                     ZL_ERR_TIMEOUT).  Reading it synchronises the device.
+ */
+zl_status zl_get_runtime_info(zl_plan plan, int* tensor_core_path, int* device_error);
+
+/*
  * zl_get_modes -- the kept packed mode indices s (ascending), host int[L].
  * Output coefficient j of every member refers to mode modes[j].
  */

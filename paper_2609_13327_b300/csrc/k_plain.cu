@@ -27,7 +27,7 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int KC = 8;                    // members per CTA in the forward pass
-constexpr size_t kRowSmemBudget = 64 * 1024;
+constexpr size_t kRowSmemBudget = 72 * 1024;
 
 // ---------------------------------------------------------------------------
 // forward, pass 1: per-column product + x-pass, CTA = (grid row y, RC rhs, KC members)
@@ -37,7 +37,8 @@ __global__ void __launch_bounds__(kThreads)
 fwd_column_xpass(const T* __restrict__ x, const T* __restrict__ M, const T* __restrict__ bx, T* __restrict__ t1,
                  int R, int nw, int K, int nx, int ny, int Px) {
     extern __shared__ unsigned char smem_raw[];
-    T* W = reinterpret_cast<T*>(smem_raw);   // [KC][RC][nx]
+    T* W = reinterpret_cast<T*>(smem_raw);   // [KC][RC][ldw]
+    const int ldw = nx + 1;
     // member chunk fastest, then rhs chunk, then grid row: the CTAs that share a
     // row's x and M tiles run back to back and find them in L2
     const int k0 = blockIdx.x * KC;
@@ -67,29 +68,58 @@ fwd_column_xpass(const T* __restrict__ x, const T* __restrict__ M, const T* __re
 #pragma unroll
         for (int k = 0; k < KC; ++k)
 #pragma unroll
-            for (int r = 0; r < RC; ++r) W[((size_t)k * RC + r) * nx + xc] = acc[r][k];
+            for (int r = 0; r < RC; ++r) W[((size_t)k * RC + r) * ldw + xc] = acc[r][k];
     }
     __syncthreads();
 
-    // x-pass: t1[r][k][y][jx] = sum_x W[k][r][x] * bx[jx][x]
-    const int nout = KC * RC * Px;
-    for (int o = threadIdx.x; o < nout; o += blockDim.x) {
-        const int jx = o % Px;
-        const int kr = o / Px;
-        const int r = kr % RC, k = kr / RC;
-        if (r0 + r >= R || k0 + k >= K) continue;
-        const T* w = W + ((size_t)k * RC + r) * nx;
-        const T* b = bx + (size_t)jx * nx;
-        T s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+    // x-pass, a small GEMM per CTA: t1[r][k][y][jx] = sum_x W[k][r][x] * bx[jx][x].
+    // Thread (rg, cg) of a 16 x 16 layout owns rows rg + 16 i (i < 4) and
+    // x-frequencies c0 + cg + 16 j (j < 3); W rows are padded to ldw = nx + 1
+    // words so the 16 rows a warp reads sit in distinct banks, and the basis
+    // rows are read from L1 with two distinct addresses per warp.
+    const int rows = KC * RC;
+    const int rg = threadIdx.x & 15, cg = threadIdx.x >> 4;
+    for (int c0 = 0; c0 < Px; c0 += 48) {
+        T acc[4][3][2];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) acc[i][j][0] = acc[i][j][1] = T(0);
+        const T* wrow[4];
+        const T* brow[3];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) wrow[i] = W + (size_t)min(rg + 16 * i, rows - 1) * ldw;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) brow[j] = bx + (size_t)min(c0 + cg + 16 * j, Px - 1) * nx;
+        auto step = [&](int xc, int h) {
+            T wv[4], bv[3];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) wv[i] = wrow[i][xc];
+#pragma unroll
+            for (int j = 0; j < 3; ++j) bv[j] = __ldg(brow[j] + xc);
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 3; ++j) acc[i][j][h] = fma(wv[i], bv[j], acc[i][j][h]);
+        };
         int xc = 0;
-        for (; xc + 3 < nx; xc += 4) {
-            s0 = fma(w[xc], b[xc], s0);
-            s1 = fma(w[xc + 1], b[xc + 1], s1);
-            s2 = fma(w[xc + 2], b[xc + 2], s2);
-            s3 = fma(w[xc + 3], b[xc + 3], s3);
+        for (; xc + 1 < nx; xc += 2) {
+            step(xc, 0);
+            step(xc + 1, 1);
         }
-        for (; xc < nx; ++xc) s0 = fma(w[xc], b[xc], s0);
-        t1[(((long long)(r0 + r) * K + k0 + k) * ny + y) * Px + jx] = (s0 + s1) + (s2 + s3);
+        if (xc < nx) step(xc, 0);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int row = rg + 16 * i;
+            const int k = row / RC, r = row - k * RC;
+            if (row >= rows || r0 + r >= R || k0 + k >= K) continue;
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                const int jx = c0 + cg + 16 * j;
+                if (jx < Px)
+                    t1[(((long long)(r0 + r) * K + k0 + k) * ny + y) * Px + jx] = acc[i][j][0] + acc[i][j][1];
+            }
+        }
     }
 }
 
@@ -100,24 +130,25 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads)
 fwd_ypass(const T* __restrict__ t1, const T* __restrict__ by, const int* __restrict__ m_py,
           const int* __restrict__ m_jx, const T* __restrict__ scale, T* __restrict__ out,
-          int K, int ny, int Px, int L, int ychunk) {
+          int K, int ny, int Px, int ldp, int L, int ychunk) {
     extern __shared__ unsigned char smem_raw[];
     T* acc = reinterpret_cast<T*>(smem_raw);   // [L]
-    T* tile = acc + L;                         // [Px][ychunk]
+    T* tile = acc + L;                         // [Px][ychunk + 1]: odd stride, conflict-free rows
+    const int ldt = ychunk + 1;
     const int k = blockIdx.x, r = blockIdx.y;
-    const T* src = t1 + ((long long)r * K + k) * ny * Px;
+    const T* src = t1 + ((long long)r * K + k) * ny * ldp;
     for (int j = threadIdx.x; j < L; j += blockDim.x) acc[j] = T(0);
     for (int y0 = 0; y0 < ny; y0 += ychunk) {
         const int yn = min(ychunk, ny - y0);
         __syncthreads();
         for (int e = threadIdx.x; e < yn * Px; e += blockDim.x) {
             const int yy = e / Px, jx = e - yy * Px;
-            tile[jx * ychunk + yy] = src[(long long)(y0 + yy) * Px + jx];
+            tile[jx * ldt + yy] = src[(long long)(y0 + yy) * ldp + jx];
         }
         __syncthreads();
         for (int j = threadIdx.x; j < L; j += blockDim.x) {
             const T* b = by + (size_t)m_py[j] * ny + y0;
-            const T* t = tile + (size_t)m_jx[j] * ychunk;
+            const T* t = tile + (size_t)m_jx[j] * ldt;
             T s0 = 0, s1 = 0;
             int yy = 0;
             for (; yy + 1 < yn; yy += 2) {
@@ -203,7 +234,7 @@ inv_xpass_column(const T* __restrict__ u, const T* __restrict__ M, const T* __re
 template <typename T, int RC>
 cudaError_t launch_fwd_rc(const zl_plan_s& p, const T* x, const T* M, const T* bx, T* t1, int R, cudaStream_t s) {
     const int nx = p.d.nx, ny = p.d.ny, K = p.d.K;
-    const size_t smem = (size_t)KC * RC * nx * sizeof(T);
+    const size_t smem = (size_t)KC * RC * (nx + 1) * sizeof(T);
     cudaError_t e = cudaFuncSetAttribute(fwd_column_xpass<T, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((K + KC - 1) / KC, (R + RC - 1) / RC, ny);
@@ -211,7 +242,27 @@ cudaError_t launch_fwd_rc(const zl_plan_s& p, const T* x, const T* M, const T* b
     return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_ypass(const zl_plan_s& p, const T* t1, int ldp, const T* by, const int* m_py, const int* m_jx,
+                         const T* scale, T* out, int R, cudaStream_t s) {
+    const int ny = p.d.ny, K = p.d.K;
+    int ychunk = ny;
+    while ((size_t)(p.L + p.Px * (ychunk + 1)) * sizeof(T) > 96 * 1024 && ychunk > 1) ychunk = (ychunk + 1) / 2;
+    const size_t smem = (size_t)(p.L + p.Px * (ychunk + 1)) * sizeof(T);
+    cudaError_t e = cudaFuncSetAttribute(fwd_ypass<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    p.timer.begin(ZL_STAGE_FWD_YPASS, s);
+    fwd_ypass<T><<<dim3(K, R), kThreads, smem, s>>>(t1, by, m_py, m_jx, scale, out, K, ny, p.Px, ldp, p.L, ychunk);
+    p.timer.end(s);
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t forward_ypass_f32(const zl_plan_s& p, const float* t1, int ldp, const float* scale, float* out, int R,
+                              cudaStream_t s) {
+    return launch_ypass<float>(p, t1, ldp, p.tf.by, p.tf.m_py, p.tf.m_jx, scale, out, R, s);
+}
 
 template <typename T>
 cudaError_t forward_plain(const zl_plan_s& p, const Tables<T>& t, const T* M, const T* scale, const T* x, T* out,
@@ -219,7 +270,7 @@ cudaError_t forward_plain(const zl_plan_s& p, const Tables<T>& t, const T* M, co
     const int nx = p.d.nx, ny = p.d.ny, K = p.d.K;
     T* t1 = reinterpret_cast<T*>(p.t1);
     cudaError_t e;
-    const size_t row = (size_t)KC * nx * sizeof(T);
+    const size_t row = (size_t)KC * (nx + 1) * sizeof(T);
     p.timer.begin(ZL_STAGE_FWD_COLUMN, s);
     if (R >= 8 && 8 * row <= kRowSmemBudget) e = launch_fwd_rc<T, 8>(p, x, M, t.bx, t1, R, s);
     else if (R >= 4 && 4 * row <= kRowSmemBudget) e = launch_fwd_rc<T, 4>(p, x, M, t.bx, t1, R, s);
@@ -228,15 +279,7 @@ cudaError_t forward_plain(const zl_plan_s& p, const Tables<T>& t, const T* M, co
     p.timer.end(s);
     if (e != cudaSuccess) return e;
 
-    int ychunk = ny;
-    while ((size_t)(p.L + p.Px * ychunk) * sizeof(T) > 96 * 1024 && ychunk > 1) ychunk = (ychunk + 1) / 2;
-    const size_t smem = (size_t)(p.L + p.Px * ychunk) * sizeof(T);
-    e = cudaFuncSetAttribute(fwd_ypass<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    p.timer.begin(ZL_STAGE_FWD_YPASS, s);
-    fwd_ypass<T><<<dim3(K, R), kThreads, smem, s>>>(t1, t.by, t.m_py, t.m_jx, scale, out, K, ny, p.Px, p.L, ychunk);
-    p.timer.end(s);
-    return cudaGetLastError();
+    return launch_ypass<T>(p, t1, p.Px, t.by, t.m_py, t.m_jx, scale, out, R, s);
 }
 
 template <typename T>

@@ -1,11 +1,613 @@
-// Tensor-core left inverse (ZL_MIXED).  Placeholder until the tcgen05 kernel lands:
-// tc_prepare reports ZL_ERR_UNSUPPORTED and the plan runs the FP32 CUDA-core passes.
+// Tensor-core left inverse (ZL_MIXED): steps V1-V3 plus the x-pass of V4 in one
+// persistent, warp-specialised tcgen05 kernel.
+//
+// Work unit = (grid row y, chunk of RC = 16 right-hand sides).  For every
+// column m of the row the per-column product of step V1 (Sec. 3.9),
+//     w^(m) = A_m^+ x^(m),   a K x n_w by n_w x RC product,
+// runs on the tensor cores with FP16 operand splits P = P_hi + P_lo and
+// x = x_hi + x_lo: the A operand stacks [P_hi; P_lo] (M = 128 rows = 2 x 64
+// members), so two MMAs (B = x_hi, then B = x_lo) leave all four partial
+// products in TMEM (rows k: P_hi x, rows 64 + k: P_lo x).  The epilogue warps
+// add the two halves, split the FP32 sum into FP16 hi/lo again and write it as
+// the A operand of the x-pass, whose rows are the (rhs, member) pairs of the
+// unit and whose K dimension runs along the grid row.  The x-pass MMA
+// multiplies by the pruned real-Fourier basis of the row (N = 48 >= Px kept
+// x-frequencies, hi/lo split, three products) and accumulates the whole row in
+// TMEM.  The regrouping of w^(m) into member segments (steps V2-V3, the
+// paper's inter-processor exchange) thus never leaves the SM.  The y-pass,
+// Delta^{-1/2} scaling and compaction (the rest of V4, and V5) follow in the
+// CUDA-core kernel fwd_ypass.
+//
+// Warp roles (192 threads): warp 0 lane 0 = TMA producer (x tiles through a
+// 3-D tensor map, the per-column [P_hi; P_lo] images by 1-D bulk copies),
+// warp 1 = TMEM allocator + single-thread MMA issuer, warps 2-5 = converters
+// (x tile -> FP16 hi/lo B operand) and epilogue (TMEM -> W operand, TMEM ->
+// intermediate t1).  All waits are bounded; on timeout the kernel records an
+// error code, drains its own copies, frees TMEM and returns.
+
 #include "zl_internal.cuh"
+#include "tc_ptx.cuh"
+
+#include <cuda.h>
+#include <cuda_fp16.h>
+
+#include <cmath>
+#include <vector>
 
 namespace zl {
 
-zl_status tc_prepare(zl_plan_s&, cudaStream_t) { return ZL_ERR_UNSUPPORTED; }
-void tc_release(zl_plan_s&) {}
-cudaError_t forward_tc(const zl_plan_s&, const float*, float*, int, cudaStream_t) { return cudaErrorNotSupported; }
+struct TcOperands {
+    __half* pimg = nullptr;    // [nh][128 rows][nwp] K-major image of [P_hi; P_lo] per column
+    __half* bximg = nullptr;   // [2 splits][nx/8 chunks][6 row groups][8][8] x-pass basis image
+    int* d_err = nullptr;      // device error word (0 = ok)
+    int nwp = 0;               // V1 K extent: n_w rounded up to 16 or 32
+    int pxp = 0;               // row stride of t1 (Px rounded up to 4)
+    int num_sms = 0;
+    uint32_t smem = 0;
+};
+
+namespace {
+
+using namespace tc;
+
+constexpr int RC = 16;                 // right-hand sides per unit (V1 N)
+constexpr int GC = 8;                  // columns per gather group (one K-chunk of the x-pass)
+constexpr int N2 = 48;                 // x-pass N: kept x-frequencies padded
+constexpr int MT = 8;                  // x-pass M tiles: 64 members x 16 rhs / 128
+constexpr int SP = 4;                  // P image ring depth
+constexpr int SX = 2;                  // x tile ring depth
+constexpr int kThreadsTc = 192;
+constexpr uint32_t kD1Col = MT * N2;   // 384: D1 (V1 accumulators) after the x-pass accumulators
+constexpr uint32_t kTmemCols = 512;
+constexpr uint32_t kWChunk = 16384;    // one 8-column K-chunk of W: 1024 rows x 16 B
+constexpr uint32_t kWSplit = 32768;    // hi / lo offset inside W
+constexpr unsigned long long kWaitCycles = 4000000000ull;   // ~2 s at 2 GHz
+
+struct SmemPlan {
+    uint32_t bx, pring, xring, b1, w, scratch, bars, total;
+};
+
+__host__ __device__ inline uint32_t b1_stride(int nwp) { return 64u * nwp + 16u; }   // hi + lo + 16 B pad
+
+__host__ __device__ inline SmemPlan smem_plan(int nx, int nwp) {
+    SmemPlan s;
+    uint32_t o = 0;
+    s.bx = o;
+    o += 2u * nx * 96u;                  // 2 splits x nx/8 chunks x 6 row groups x 128 B
+    s.pring = o;
+    o += SP * 256u * nwp;                // 128 rows x nwp x 2 B
+    s.xring = o;
+    o += SX * 512u * nwp;                // RC x nwp x GC x 4 B
+    s.b1 = o;
+    o += GC * b1_stride(nwp);
+    o = (o + 127u) & ~127u;
+    s.w = o;
+    o += 2 * kWSplit;
+    s.scratch = o;
+    o += 16384;
+    s.bars = o;
+    o += 256;
+    s.total = o;
+    return s;
+}
+
+// Barrier slots
+enum {
+    B_PFULL = 0,
+    B_PEMPTY = B_PFULL + SP,
+    B_XFULL = B_PEMPTY + SP,
+    B_XEMPTY = B_XFULL + SX,
+    B_B1FULL = B_XEMPTY + SX,
+    B_B1EMPTY,
+    B_D1FULL,
+    B_D1EMPTY,
+    B_WFULL,
+    B_WEMPTY,
+    B_D2FULL,
+    B_D2EMPTY,
+    B_EX0,
+    B_EX1,
+    B_FIN,
+    B_COUNT
+};
+
+__device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+    const long long t0 = clock64();
+    for (uint32_t i = 0;; ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((i & 255u) == 255u) {
+            if (*abort_flag) return false;
+            if ((unsigned long long)(clock64() - t0) > kWaitCycles) return false;
+        }
+    }
+}
+
+// Wait used by whole warps before warp-collective tcgen05.ld: the outcome is made warp-uniform.
+__device__ __forceinline__ bool warp_wait_bar(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+    const bool ok = wait_bar(bar, parity, abort_flag);
+    return __all_sync(0xffffffffu, ok);
+}
+
+__device__ __forceinline__ void fail(volatile int* abort_flag, int* err, int code) {
+    *abort_flag = 1;
+    atomicCAS(err, 0, code);
+}
+
+__device__ __forceinline__ void split2(float a, float b, uint32_t& hi, uint32_t& lo) {
+    const __half2 h = __floats2half2_rn(a, b);
+    const float2 hf = __half22float2(h);
+    const __half2 l = __floats2half2_rn(a - hf.x, b - hf.y);
+    hi = *reinterpret_cast<const uint32_t*>(&h);
+    lo = *reinterpret_cast<const uint32_t*>(&l);
+}
+
+__global__ void __launch_bounds__(kThreadsTc, 1)
+fwd_column_tc_kernel(const __grid_constant__ CUtensorMap tmap_x, const __half* __restrict__ pimg,
+                     const __half* __restrict__ bximg, float* __restrict__ t1, int* __restrict__ err,
+                     int R, int K, int nx, int ny, int nwp, int Px, int pxp) {
+    extern __shared__ __align__(1024) uint8_t smem[];
+    const SmemPlan sp = smem_plan(nx, nwp);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + sp.bars);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + B_COUNT);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
+    uint8_t* sbx = smem + sp.bx;
+    uint8_t* spring = smem + sp.pring;
+    uint8_t* sxring = smem + sp.xring;
+    uint8_t* sb1 = smem + sp.b1;
+    uint8_t* sw = smem + sp.w;
+    float4* sscr = reinterpret_cast<float4*>(smem + sp.scratch);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int n_rc = (R + RC - 1) / RC;
+    const int units = ny * n_rc;
+    const int G = nx / GC;
+    const uint32_t PBYTES = 256u * nwp;
+    const uint32_t XBYTES = 512u * nwp;
+    const uint32_t B1S = b1_stride(nwp);
+    const uint32_t b1_sbo = (uint32_t)(nwp / 8) * 128u;
+
+    if (tid == 0) {
+        for (int i = 0; i < SP; ++i) {
+            mbar_init(&bars[B_PFULL + i], 1);
+            mbar_init(&bars[B_PEMPTY + i], 1);
+        }
+        for (int i = 0; i < SX; ++i) {
+            mbar_init(&bars[B_XFULL + i], 1);
+            mbar_init(&bars[B_XEMPTY + i], 128);
+        }
+        mbar_init(&bars[B_B1FULL], 128);
+        mbar_init(&bars[B_B1EMPTY], 1);
+        mbar_init(&bars[B_D1FULL], 1);
+        mbar_init(&bars[B_D1EMPTY], 128);
+        mbar_init(&bars[B_WFULL], 128);
+        mbar_init(&bars[B_WEMPTY], 1);
+        mbar_init(&bars[B_D2FULL], 1);
+        mbar_init(&bars[B_D2EMPTY], 128);
+        mbar_init(&bars[B_EX0], 128);
+        mbar_init(&bars[B_EX1], 128);
+        mbar_init(&bars[B_FIN], 1);
+        *abort_flag = 0;
+        fence_mbar_init();
+        prefetch_tmap(&tmap_x);
+    }
+    if (warp == 1) tmem_alloc(tslot, kTmemCols);
+    // the x-pass basis image is the same for every row: load it once
+    {
+        const int4* src = reinterpret_cast<const int4*>(bximg);
+        int4* dst = reinterpret_cast<int4*>(sbx);
+        const int n16 = (int)(2u * nx * 96u / 16u);
+        for (int i = tid; i < n16; i += blockDim.x) dst[i] = src[i];
+        fence_proxy_async_smem();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = *tslot;
+
+    if (warp == 0) {
+        // ------------------------------------------------------------ producer
+        if (lane == 0) {
+            uint32_t pc = 0, xc = 0;
+            bool ok = true;
+            for (int u = blockIdx.x; u < units && ok; u += gridDim.x) {
+                const int y = u / n_rc, r0 = (u % n_rc) * RC;
+                for (int g = 0; g < G && ok; ++g) {
+                    const uint32_t xs = xc % SX, xph = (xc / SX) & 1u;
+                    if (!wait_bar(&bars[B_XEMPTY + xs], xph ^ 1u, abort_flag)) { fail(abort_flag, err, 1); ok = false; break; }
+                    mbar_arrive_expect_tx(&bars[B_XFULL + xs], XBYTES);
+                    tma_load_3d(sxring + xs * XBYTES, &tmap_x, y * nx + g * GC, 0, r0, &bars[B_XFULL + xs]);
+                    ++xc;
+                    for (int j = 0; j < GC; ++j) {
+                        const uint32_t ps = pc % SP, pph = (pc / SP) & 1u;
+                        if (!wait_bar(&bars[B_PEMPTY + ps], pph ^ 1u, abort_flag)) { fail(abort_flag, err, 1); ok = false; break; }
+                        mbar_arrive_expect_tx(&bars[B_PFULL + ps], PBYTES);
+                        const size_t col = (size_t)y * nx + (size_t)g * GC + j;
+                        bulk_g2s(spring + ps * PBYTES, pimg + col * 128u * nwp, PBYTES, &bars[B_PFULL + ps]);
+                        ++pc;
+                    }
+                }
+            }
+            // drain: every issued copy must land before the CTA exits
+            for (uint32_t s = 0; s < SP; ++s) {
+                if (pc > s) {
+                    const uint32_t nissued = (pc - s + SP - 1) / SP;   // loads issued into slot s
+                    const uint32_t par = (nissued - 1) & 1u;
+                    const long long t0 = clock64();
+                    while (!mbar_try_wait(&bars[B_PFULL + s], par) && (unsigned long long)(clock64() - t0) < kWaitCycles) {}
+                }
+            }
+            for (uint32_t s = 0; s < SX; ++s) {
+                if (xc > s) {
+                    const uint32_t nissued = (xc - s + SX - 1) / SX;
+                    const uint32_t par = (nissued - 1) & 1u;
+                    const long long t0 = clock64();
+                    while (!mbar_try_wait(&bars[B_XFULL + s], par) && (unsigned long long)(clock64() - t0) < kWaitCycles) {}
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            const uint32_t idesc_v1 = idesc_f16_f32(128, RC);
+            const uint32_t idesc_x = idesc_f16_f32(128, N2);
+            const uint32_t a_sbo = (uint32_t)(nwp / 8) * 128u;
+            const uint32_t bx_lbo = 6u * 128u;
+            const uint32_t bx_split = (uint32_t)(nx / 8) * bx_lbo;
+            uint32_t pc = 0, gc = 0, kc = 0, uc = 0;
+            bool ok = true;
+            for (int u = blockIdx.x; u < units && ok; u += gridDim.x) {
+                for (int g = 0; g < G && ok; ++g) {
+                    if (!wait_bar(&bars[B_B1FULL], gc & 1u, abort_flag) ||
+                        !wait_bar(&bars[B_D1EMPTY], (gc & 1u) ^ 1u, abort_flag)) { fail(abort_flag, err, 2); ok = false; break; }
+                    tc_fence_after();
+                    for (int j = 0; j < GC; ++j) {
+                        const uint32_t ps = pc % SP, pph = (pc / SP) & 1u;
+                        if (!wait_bar(&bars[B_PFULL + ps], pph, abort_flag)) { fail(abort_flag, err, 2); ok = false; break; }
+                        tc_fence_after();
+                        const uint32_t a0 = smem_u32(spring + ps * PBYTES);
+                        const uint32_t bhi = smem_u32(sb1 + j * B1S);
+                        const uint32_t blo = bhi + 32u * nwp;
+                        const uint32_t d = tbase + kD1Col + (uint32_t)j * RC;
+                        for (int ks = 0; ks < nwp / 16; ++ks)
+                            mma_f16(d, smem_desc(a0 + ks * 256u, 128u, a_sbo), smem_desc(bhi + ks * 256u, 128u, b1_sbo),
+                                    idesc_v1, ks > 0);
+                        for (int ks = 0; ks < nwp / 16; ++ks)
+                            mma_f16(d, smem_desc(a0 + ks * 256u, 128u, a_sbo), smem_desc(blo + ks * 256u, 128u, b1_sbo),
+                                    idesc_v1, 1u);
+                        mma_commit(&bars[B_PEMPTY + ps]);
+                        ++pc;
+                    }
+                    if (!ok) break;
+                    mma_commit(&bars[B_D1FULL]);
+                    mma_commit(&bars[B_B1EMPTY]);
+                    ++gc;
+                    if (g & 1) {
+                        const int s = g >> 1;
+                        if (!wait_bar(&bars[B_WFULL], kc & 1u, abort_flag)) { fail(abort_flag, err, 2); ok = false; break; }
+                        if (s == 0 && !wait_bar(&bars[B_D2EMPTY], (uc & 1u) ^ 1u, abort_flag)) { fail(abort_flag, err, 2); ok = false; break; }
+                        tc_fence_after();
+                        const uint32_t bhi = smem_u32(sbx) + (uint32_t)s * 2u * bx_lbo;
+                        const uint32_t blo = bhi + bx_split;
+                        const uint64_t dbhi = smem_desc(bhi, bx_lbo, 128u), dblo = smem_desc(blo, bx_lbo, 128u);
+                        for (int t = 0; t < MT; ++t) {
+                            const uint32_t ahi = smem_u32(sw) + (uint32_t)t * 2048u;
+                            const uint64_t dahi = smem_desc(ahi, kWChunk, 128u), dalo = smem_desc(ahi + kWSplit, kWChunk, 128u);
+                            const uint32_t d = tbase + (uint32_t)t * N2;
+                            mma_f16(d, dahi, dbhi, idesc_x, s > 0);
+                            mma_f16(d, dalo, dbhi, idesc_x, 1u);
+                            mma_f16(d, dahi, dblo, idesc_x, 1u);
+                        }
+                        mma_commit(&bars[B_WEMPTY]);
+                        ++kc;
+                    }
+                }
+                if (!ok) break;
+                mma_commit(&bars[B_D2FULL]);
+                ++uc;
+            }
+            mma_commit(&bars[B_FIN]);
+            const long long t0 = clock64();
+            while (!mbar_try_wait(&bars[B_FIN], 0) && (unsigned long long)(clock64() - t0) < kWaitCycles) {}
+        }
+    } else {
+        // ------------------------------------------------------------ converters + epilogue
+        const int et = tid - 64;                 // 0..127
+        const int q = warp & 3;                  // TMEM lane quarter this warp may access
+        const uint32_t lane_off = (uint32_t)(32 * q) << 16;
+        const bool top = q < 2;                  // lanes 0-63: P_hi x;  lanes 64-127: P_lo x
+        const int kk = (q & 1) * 32 + lane;      // member of this thread's TMEM lane
+        const int my_r0 = top ? 0 : 8, other_r0 = top ? 8 : 0;
+        const int region = q & 1;
+        uint32_t xc = 0, cc = 0, gc = 0, kc = 0, uc = 0, exc = 0;
+        bool ok = true;
+
+        auto convert = [&](int) -> bool {
+            const uint32_t xs = xc % SX, xph = (xc / SX) & 1u;
+            if (!warp_wait_bar(&bars[B_XFULL + xs], xph, abort_flag)) return false;
+            if (!warp_wait_bar(&bars[B_B1EMPTY], (cc & 1u) ^ 1u, abort_flag)) return false;
+            const float* xt = reinterpret_cast<const float*>(sxring + xs * XBYTES);   // [r][l][m] = [RC][nwp][GC]
+            const int noct = nwp / 8;
+            for (int item = et; item < GC * RC * noct; item += 128) {
+                const int j = item % GC, rest = item / GC;
+                const int o = rest % noct, r = rest / noct;
+                float v[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) v[i] = xt[(r * nwp + 8 * o + i) * GC + j];
+                uint4 hi, lo;
+                split2(v[0], v[1], hi.x, lo.x);
+                split2(v[2], v[3], hi.y, lo.y);
+                split2(v[4], v[5], hi.z, lo.z);
+                split2(v[6], v[7], hi.w, lo.w);
+                uint8_t* dst = sb1 + j * B1S + (r >> 3) * b1_sbo + o * 128u + (r & 7) * 16u;
+                *reinterpret_cast<uint4*>(dst) = hi;
+                *reinterpret_cast<uint4*>(dst + 32u * nwp) = lo;
+            }
+            fence_proxy_async_smem();
+            mbar_arrive(&bars[B_B1FULL]);
+            mbar_arrive(&bars[B_XEMPTY + xs]);
+            ++xc;
+            ++cc;
+            return true;
+        };
+
+        for (int u = blockIdx.x; u < units && ok; u += gridDim.x) {
+            const int y = u / n_rc, r0 = (u % n_rc) * RC;
+            if (!convert(0)) { fail(abort_flag, err, 3); ok = false; break; }
+            for (int g = 0; g < G && ok; ++g) {
+                if (g + 1 < G && !convert(g + 1)) { fail(abort_flag, err, 3); ok = false; break; }
+                // ---- drain D1 of group g: exchange halves, sum, split, write W
+                if (!warp_wait_bar(&bars[B_D1FULL], gc & 1u, abort_flag)) { fail(abort_flag, err, 3); ok = false; break; }
+                tc_fence_after();
+                float acc[GC][8];
+#pragma unroll
+                for (int pass = 0; pass < 2; ++pass) {
+                    if (!ok) break;
+#pragma unroll
+                    for (int jj = 0; jj < 4; ++jj) {
+                        const int j = 4 * pass + jj;
+                        uint32_t v[8];
+                        tmem_ld8(tbase + lane_off + kD1Col + (uint32_t)(j * RC + other_r0), v);
+                        tmem_ld_wait();
+                        float4* slot = sscr + ((((region * 2 + (top ? 0 : 1)) * 4 + jj) * 2) * 32);
+                        slot[lane] = make_float4(__uint_as_float(v[0]), __uint_as_float(v[1]), __uint_as_float(v[2]), __uint_as_float(v[3]));
+                        slot[32 + lane] = make_float4(__uint_as_float(v[4]), __uint_as_float(v[5]), __uint_as_float(v[6]), __uint_as_float(v[7]));
+                    }
+                    mbar_arrive(&bars[B_EX0]);
+                    if (!warp_wait_bar(&bars[B_EX0], exc & 1u, abort_flag)) { fail(abort_flag, err, 3); ok = false; break; }
+#pragma unroll
+                    for (int jj = 0; jj < 4; ++jj) {
+                        const int j = 4 * pass + jj;
+                        uint32_t v[8];
+                        tmem_ld8(tbase + lane_off + kD1Col + (uint32_t)(j * RC + my_r0), v);
+                        tmem_ld_wait();
+                        const float4* slot = sscr + ((((region * 2 + (top ? 1 : 0)) * 4 + jj) * 2) * 32);
+                        const float4 a = slot[lane], b = slot[32 + lane];
+                        acc[j][0] = __uint_as_float(v[0]) + a.x;
+                        acc[j][1] = __uint_as_float(v[1]) + a.y;
+                        acc[j][2] = __uint_as_float(v[2]) + a.z;
+                        acc[j][3] = __uint_as_float(v[3]) + a.w;
+                        acc[j][4] = __uint_as_float(v[4]) + b.x;
+                        acc[j][5] = __uint_as_float(v[5]) + b.y;
+                        acc[j][6] = __uint_as_float(v[6]) + b.z;
+                        acc[j][7] = __uint_as_float(v[7]) + b.w;
+                    }
+                    mbar_arrive(&bars[B_EX1]);
+                    if (!warp_wait_bar(&bars[B_EX1], exc & 1u, abort_flag)) { fail(abort_flag, err, 3); ok = false; break; }
+                    ++exc;
+                }
+                if (!ok) break;
+                tc_fence_before();
+                mbar_arrive(&bars[B_D1EMPTY]);
+                ++gc;
+                const int chunk = g & 1;
+                if (chunk == 0 && !warp_wait_bar(&bars[B_WEMPTY], (kc & 1u) ^ 1u, abort_flag)) { fail(abort_flag, err, 3); ok = false; break; }
+#pragma unroll
+                for (int rl = 0; rl < 8; ++rl) {
+                    const int r = my_r0 + rl;
+                    uint4 hi, lo;
+                    split2(acc[0][rl], acc[1][rl], hi.x, lo.x);
+                    split2(acc[2][rl], acc[3][rl], hi.y, lo.y);
+                    split2(acc[4][rl], acc[5][rl], hi.z, lo.z);
+                    split2(acc[6][rl], acc[7][rl], hi.w, lo.w);
+                    const uint32_t row = (uint32_t)r * 64u + (uint32_t)kk;
+                    const uint32_t off = (uint32_t)chunk * kWChunk + (row >> 3) * 128u + (row & 7u) * 16u;
+                    *reinterpret_cast<uint4*>(sw + off) = hi;
+                    *reinterpret_cast<uint4*>(sw + kWSplit + off) = lo;
+                }
+                fence_proxy_async_smem();
+                if (chunk == 1) {
+                    mbar_arrive(&bars[B_WFULL]);
+                    ++kc;
+                }
+            }
+            if (!ok) break;
+            // ---- drain D2: the row's x-pass, rows (r, k) -> t1[r0 + r][k][y][0..pxp)
+            if (!warp_wait_bar(&bars[B_D2FULL], uc & 1u, abort_flag)) { fail(abort_flag, err, 3); ok = false; break; }
+            tc_fence_after();
+            for (int t = 0; t < MT; ++t) {
+                const int row = 128 * t + 32 * q + lane;
+                const int r = row >> 6, k = row & 63;
+                uint32_t v[16 * 3];
+                tmem_ld16(tbase + lane_off + (uint32_t)(t * N2), *reinterpret_cast<uint32_t(*)[16]>(&v[0]));
+                tmem_ld16(tbase + lane_off + (uint32_t)(t * N2 + 16), *reinterpret_cast<uint32_t(*)[16]>(&v[16]));
+                tmem_ld16(tbase + lane_off + (uint32_t)(t * N2 + 32), *reinterpret_cast<uint32_t(*)[16]>(&v[32]));
+                tmem_ld_wait();
+                if (r0 + r < R && k < K) {
+                    float4* dst = reinterpret_cast<float4*>(t1 + (((size_t)(r0 + r) * K + k) * ny + y) * pxp);
+#pragma unroll
+                    for (int c = 0; c < N2 / 4; ++c)
+                        if (4 * c < pxp)
+                            dst[c] = make_float4(__uint_as_float(v[4 * c]), __uint_as_float(v[4 * c + 1]),
+                                                 __uint_as_float(v[4 * c + 2]), __uint_as_float(v[4 * c + 3]));
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(&bars[B_D2EMPTY]);
+            ++uc;
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1) {
+        __syncwarp();
+        tmem_dealloc(tbase, kTmemCols);
+    }
+}
+
+// Pseudo-inverse image: pimg[m][row][l] in the K-major core-matrix layout,
+// row < 64: P_hi[k = row], row >= 64: P_lo[k = row - 64]; zero outside K x n_w.
+__global__ void build_pimg_kernel(const float* __restrict__ P, __half* __restrict__ pimg, int K, int nw, int nwp,
+                                  long long nh) {
+    const long long total = nh * 64 * nwp;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        const int l = (int)(i % nwp);
+        const int k = (int)((i / nwp) % 64);
+        const long long m = i / ((long long)nwp * 64);
+        const float v = (k < K && l < nw) ? P[((long long)k * nw + l) * nh + m] : 0.f;
+        const __half hi = __float2half_rn(v);
+        const __half lo = __float2half_rn(v - __half2float(hi));
+        uint8_t* base = reinterpret_cast<uint8_t*>(pimg) + (size_t)m * 256u * nwp;
+        const uint32_t sbo = (uint32_t)(nwp / 8) * 128u;
+        *reinterpret_cast<__half*>(base + kmajor_offset((uint32_t)k, (uint32_t)l, 128u, sbo)) = hi;
+        *reinterpret_cast<__half*>(base + kmajor_offset((uint32_t)(k + 64), (uint32_t)l, 128u, sbo)) = lo;
+    }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
+double basis_value_d(int N, int p, int m) {
+    if (p == 0) return 1.0 / std::sqrt((double)N);
+    if (N % 2 == 0 && p == N - 1) return ((m & 1) ? -1.0 : 1.0) / std::sqrt((double)N);
+    const int j = (p + 1) / 2;
+    const long long r = ((long long)j * m) % N;
+    const double a = 2.0 * M_PI * (double)r / (double)N;
+    return std::sqrt(2.0 / N) * ((p & 1) ? std::cos(a) : std::sin(a));
+}
+
+}  // namespace
+
+bool tc_supported(const zl_plan_s& p) {
+    return p.d.nx % 16 == 0 && p.d.nx <= 256 && p.d.K <= 64 && p.d.nw <= 32 && p.Px <= N2 && p.nh % 4 == 0;
+}
+
+zl_status tc_prepare(zl_plan_s& p, cudaStream_t s) {
+    if (!tc_supported(p) || encode_fn() == nullptr) return ZL_ERR_UNSUPPORTED;
+    int dev = 0, sms = 0, cc_major = 0, cc_minor = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return ZL_ERR_CUDA;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&cc_major, cudaDevAttrComputeCapabilityMajor, dev);
+    cudaDeviceGetAttribute(&cc_minor, cudaDevAttrComputeCapabilityMinor, dev);
+    if (cc_major != 10) return ZL_ERR_UNSUPPORTED;
+    TcOperands* t = new TcOperands();
+    t->nwp = p.d.nw <= 16 ? 16 : 32;
+    t->pxp = (p.Px + 3) / 4 * 4;
+    t->num_sms = sms;
+    t->smem = smem_plan(p.d.nx, t->nwp).total;
+    const int nx = p.d.nx;
+    cudaError_t e = cudaSuccess;
+    const size_t pimg_bytes = (size_t)p.nh * 256u * t->nwp;
+    const size_t bx_bytes = 2u * nx * 96u;
+    e = cudaMalloc(&t->pimg, pimg_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&t->bximg, bx_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&t->d_err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(t->pimg, 0, pimg_bytes, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(t->d_err, 0, sizeof(int), s);
+    if (e == cudaSuccess) {
+        build_pimg_kernel<<<1184, 256, 0, s>>>(reinterpret_cast<const float*>(p.P), t->pimg, p.d.K, p.d.nw, t->nwp, p.nh);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        // x-pass basis image: rows jx < Px hold b_{p_x}(x) of the kept x-frequencies
+        std::vector<__half> img(bx_bytes / 2, __float2half_rn(0.f));
+        for (int split = 0; split < 2; ++split)
+            for (int jx = 0; jx < p.Px; ++jx)
+                for (int x = 0; x < nx; ++x) {
+                    const double b = basis_value_d(nx, p.xfreq[jx], x);
+                    const __half hi = __double2half(b);
+                    const __half v = split == 0 ? hi : __double2half(b - (double)__half2float(hi));
+                    const size_t off = (size_t)split * nx * 96u + kmajor_offset((uint32_t)jx, (uint32_t)x, 768u, 128u);
+                    img[off / 2] = v;
+                }
+        e = cudaMemcpyAsync(t->bximg, img.data(), bx_bytes, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    }
+    // t1 rows are padded to pxp for 16-byte stores
+    if (e == cudaSuccess && t->pxp != p.Px) {
+        void* t1 = nullptr;
+        e = cudaMalloc(&t1, (size_t)p.d.max_rhs * p.d.K * p.d.ny * t->pxp * sizeof(float));
+        if (e == cudaSuccess) {
+            cudaFree(p.t1);
+            p.t1 = t1;
+        }
+    }
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(fwd_column_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t->smem);
+    if (e != cudaSuccess) {
+        cudaFree(t->pimg);
+        cudaFree(t->bximg);
+        cudaFree(t->d_err);
+        delete t;
+        return e == cudaErrorMemoryAllocation ? ZL_ERR_ALLOC : ZL_ERR_CUDA;
+    }
+    p.tc = t;
+    return ZL_OK;
+}
+
+void tc_release(zl_plan_s& p) {
+    if (!p.tc) return;
+    cudaFree(p.tc->pimg);
+    cudaFree(p.tc->bximg);
+    cudaFree(p.tc->d_err);
+    delete p.tc;
+    p.tc = nullptr;
+}
+
+int tc_t1_stride(const zl_plan_s& p) { return p.tc ? p.tc->pxp : p.Px; }
+
+cudaError_t tc_read_error(const zl_plan_s& p, int* code) {
+    *code = 0;
+    if (!p.tc) return cudaSuccess;
+    return cudaMemcpy(code, p.tc->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+}
+
+cudaError_t forward_tc(const zl_plan_s& p, const float* x, float* out, int R, cudaStream_t s) {
+    const TcOperands& t = *p.tc;
+    CUtensorMap tmap;
+    const cuuint64_t gdim[3] = {(cuuint64_t)p.nh, (cuuint64_t)p.d.nw, (cuuint64_t)R};
+    const cuuint64_t gstride[2] = {(cuuint64_t)p.nh * sizeof(float), (cuuint64_t)p.nh * p.d.nw * sizeof(float)};
+    const cuuint32_t box[3] = {(cuuint32_t)GC, (cuuint32_t)t.nwp, (cuuint32_t)RC};
+    const cuuint32_t estride[3] = {1, 1, 1};
+    const CUresult cr = encode_fn()(&tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(x), gdim, gstride, box,
+                                    estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (cr != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    const int units = p.d.ny * ((R + RC - 1) / RC);
+    const int grid = units < t.num_sms ? units : t.num_sms;
+    p.timer.begin(ZL_STAGE_FWD_COLUMN, s);
+    fwd_column_tc_kernel<<<grid, kThreadsTc, t.smem, s>>>(tmap, t.pimg, t.bximg, reinterpret_cast<float*>(p.t1),
+                                                          t.d_err, R, p.d.K, p.d.nx, p.d.ny, t.nwp, p.Px, t.pxp);
+    p.timer.end(s);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return forward_ypass_f32(p, reinterpret_cast<const float*>(p.t1), t.pxp, p.tf.inv_sqrt_lam, out, R, s);
+}
 
 }  // namespace zl

@@ -308,6 +308,7 @@ zl_status zl_setup(const zl_desc* desc, const void* Z, const double* spectrum, v
     for (int q = 0; q < d.nx; ++q)
         if (used[q]) xfreq.push_back(q);
     p->Px = (int)xfreq.size();
+    p->xfreq = xfreq;
     // forward y-pass keeps the L accumulators in shared memory
     if ((size_t)p->L * p->esize + (size_t)p->Px * p->esize > 96 * 1024 ||
         (size_t)d.K * (p->Px + 32) * p->esize > 160 * 1024) {
@@ -363,6 +364,18 @@ zl_status zl_get_info(zl_plan p, int* L, int* nw, int* K, long long* nh, int* ba
     if (K) *K = p->d.K;
     if (nh) *nh = p->nh;
     if (bad_column) *bad_column = p->bad_column;
+    return ZL_OK;
+}
+
+zl_status zl_get_runtime_info(zl_plan p, int* tensor_core_path, int* device_error) {
+    if (!valid_plan(p)) return ZL_ERR_ARG;
+    if (tensor_core_path) *tensor_core_path = p->tc != nullptr ? 1 : 0;
+    if (device_error) {
+        int code = 0;
+        if (zl::tc_read_error(*p, &code) != cudaSuccess) return ZL_ERR_CUDA;
+        *device_error = code;
+        if (code != 0) return ZL_ERR_TIMEOUT;
+    }
     return ZL_OK;
 }
 

@@ -56,6 +56,7 @@ struct zl_plan_s {
     int Px = 0;             // kept x-frequencies
     int bad_column = -1;
     std::vector<int> modes; // kept packed indices (host copy)
+    std::vector<int> xfreq; // kept x-frequencies (packed x-index), in the order of the x-pass
     size_t esize = 0;       // element size of caller buffers (8 or 4)
 
     // member matrices, [K][nw][nh]: the plan's copy of Z and the pseudo-inverse P (P[k][l][m] = (A_m^+)[k][l])
@@ -90,9 +91,15 @@ template <typename T>
 cudaError_t inverse_plain(const zl_plan_s& p, const Tables<T>& t, const T* M, const T* scale, const T* c, T* out,
                           int R, cudaStream_t s);
 
+// y-pass of the forward transform on an FP32 intermediate with row stride ldp
+cudaError_t forward_ypass_f32(const zl_plan_s& p, const float* t1, int ldp, const float* scale, float* out, int R,
+                              cudaStream_t s);
+
 // k_tc.cu: tensor-core left inverse (ZL_MIXED)
+bool tc_supported(const zl_plan_s& p);
 zl_status tc_prepare(zl_plan_s& p, cudaStream_t s);
 void tc_release(zl_plan_s& p);
 cudaError_t forward_tc(const zl_plan_s& p, const float* x, float* out, int R, cudaStream_t s);
+cudaError_t tc_read_error(const zl_plan_s& p, int* code);
 
 }  // namespace zl

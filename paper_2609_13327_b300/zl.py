@@ -27,7 +27,7 @@ PRECISIONS = {"fp64": ZL_FP64, "fp32": ZL_FP32, "mixed": ZL_MIXED}
 # every symbol declared in include/zl.h
 EXPORTS = ["zl_setup", "zl_get_info", "zl_get_modes", "zl_apply_left_inverse", "zl_apply_left_inverse_host",
            "zl_apply_sqrt", "zl_apply_adjoint", "zl_apply_sqrt_adjoint", "zl_destroy", "zl_status_string",
-           "zl_gaussian_spectrum", "zl_set_stage_timing", "zl_get_stage_times"]
+           "zl_gaussian_spectrum", "zl_set_stage_timing", "zl_get_stage_times", "zl_get_runtime_info"]
 STAGES = {"fwd_column": 0, "fwd_ypass": 1, "inv_ypass": 2, "inv_column": 3}
 
 
@@ -49,6 +49,7 @@ _lib.zl_status_string.argtypes = [_int]
 _lib.zl_status_string.restype = ctypes.c_char_p
 _lib.zl_gaussian_spectrum.argtypes = [_int, _int, ctypes.c_double, _dp]
 _lib.zl_set_stage_timing.argtypes = [_vp, _int]
+_lib.zl_get_runtime_info.argtypes = [_vp, _ip, _ip]
 _lib.zl_get_stage_times.argtypes = [_vp, _int, _ip, _dp]
 for _name in EXPORTS:
     if _name != "zl_status_string":
@@ -106,6 +107,20 @@ class Plan:
         out = np.empty(self.L, dtype=np.int32)
         _check(_lib.zl_get_modes(self.handle, out.ctypes.data_as(_ip)), "zl_get_modes")
         return out
+
+    def uses_tc(self):
+        """True if the left inverse runs the tcgen05 tensor-core kernel."""
+        f = _int()
+        _check(_lib.zl_get_runtime_info(self.handle, ctypes.byref(f), None), "zl_get_runtime_info")
+        return bool(f.value)
+
+    def device_error(self):
+        """0, or the code of a bounded device wait that gave up (synchronises the device)."""
+        code = _int()
+        rc = _lib.zl_get_runtime_info(self.handle, None, ctypes.byref(code))
+        if rc not in (ZL_OK, ZL_ERR_TIMEOUT):
+            _check(rc, "zl_get_runtime_info")
+        return code.value
 
     def set_stage_timing(self, enable):
         _check(_lib.zl_set_stage_timing(self.handle, 1 if enable else 0), "zl_set_stage_timing")

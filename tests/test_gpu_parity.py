@@ -176,6 +176,8 @@ def test_full_size_left_inverse_sampled(zl, name, prec, sample):
     x = synth.rhs(w, dtype=np.float32)
     out = zl.zl_apply_left_inverse(c.plan, torch.from_numpy(x).cuda()).cpu().numpy()
     assert np.all(np.isfinite(out))
+    if prec == "mixed":
+        assert c.plan.uses_tc() and c.plan.device_error() == 0
     ref = swift.apply_left_inverse(c.oracle, x[sample].astype(np.float64))
     assert rel_err(out[sample].astype(np.float64), ref) <= TOL[prec]
 
