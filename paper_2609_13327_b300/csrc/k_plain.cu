@@ -117,7 +117,7 @@ fwd_column_xpass(const T* __restrict__ x, const T* __restrict__ M, const T* __re
             for (int j = 0; j < 3; ++j) {
                 const int jx = c0 + cg + 16 * j;
                 if (jx < Px)
-                    t1[(((long long)(r0 + r) * K + k0 + k) * ny + y) * Px + jx] = acc[i][j][0] + acc[i][j][1];
+                    t1[(((long long)y * R + r0 + r) * K + k0 + k) * Px + jx] = acc[i][j][0] + acc[i][j][1];
             }
         }
     }
@@ -130,20 +130,21 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads)
 fwd_ypass(const T* __restrict__ t1, const T* __restrict__ by, const int* __restrict__ m_py,
           const int* __restrict__ m_jx, const T* __restrict__ scale, T* __restrict__ out,
-          int K, int ny, int Px, int ldp, int L, int ychunk) {
+          int R, int K, int ny, int Px, int ldp, int L, int ychunk) {
     extern __shared__ unsigned char smem_raw[];
     T* acc = reinterpret_cast<T*>(smem_raw);   // [L]
     T* tile = acc + L;                         // [Px][ychunk + 1]: odd stride, conflict-free rows
     const int ldt = ychunk + 1;
     const int k = blockIdx.x, r = blockIdx.y;
-    const T* src = t1 + ((long long)r * K + k) * ny * ldp;
+    const T* src = t1 + ((long long)r * K + k) * ldp;
+    const long long ystride = (long long)R * K * ldp;
     for (int j = threadIdx.x; j < L; j += blockDim.x) acc[j] = T(0);
     for (int y0 = 0; y0 < ny; y0 += ychunk) {
         const int yn = min(ychunk, ny - y0);
         __syncthreads();
         for (int e = threadIdx.x; e < yn * Px; e += blockDim.x) {
             const int yy = e / Px, jx = e - yy * Px;
-            tile[jx * ldt + yy] = src[(long long)(y0 + yy) * ldp + jx];
+            tile[jx * ldt + yy] = src[(long long)(y0 + yy) * ystride + jx];
         }
         __syncthreads();
         for (int j = threadIdx.x; j < L; j += blockDim.x) {
@@ -242,17 +243,95 @@ cudaError_t launch_fwd_rc(const zl_plan_s& p, const T* x, const T* M, const T* b
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// forward, pass 2 (general form): y-pass as a batched small GEMM per (rhs, member)
+// pair, OUT[p_y][jx] = sum_y b_{p_y}(y) t1[y][pair][jx], then scale + compaction.
+// Thread = (pair, jx); the kept y-basis rows are staged in shared memory and
+// broadcast; t1 rows are read coalesced across the (pair, jx) threads.
+// ---------------------------------------------------------------------------
+constexpr int kYChunk = 64;
+
+template <typename T, int PYT>
+__global__ void __launch_bounds__(kThreads)
+fwd_ypass_gemm(const T* __restrict__ t1, const T* __restrict__ byk, const int* __restrict__ m_ipy,
+               const int* __restrict__ m_jx, const T* __restrict__ scale, T* __restrict__ out,
+               int npairs, int ppc, int ny, int Px, int ldp, int L, int pys) {
+    extern __shared__ unsigned char smem_raw[];
+    T* sby = reinterpret_cast<T*>(smem_raw);       // [kYChunk][PYT]
+    T* sout = sby + kYChunk * PYT;                   // [ppc][PYT][Px]
+    const int tid = threadIdx.x;
+    const int pl = tid / Px, jx = tid - pl * Px;
+    const long long pair = (long long)blockIdx.x * ppc + pl;
+    const bool active = pl < ppc && pair < npairs;
+    const long long ystride = (long long)npairs * ldp;
+    const T* src = t1 + (active ? pair * ldp + jx : 0);
+    T acc[PYT];
+#pragma unroll
+    for (int i = 0; i < PYT; ++i) acc[i] = T(0);
+    for (int y0 = 0; y0 < ny; y0 += kYChunk) {
+        const int yn = min(kYChunk, ny - y0);
+        __syncthreads();
+        for (int e = tid; e < yn * PYT; e += blockDim.x) {
+            const int yy = e / PYT, i = e - yy * PYT;
+            sby[e] = i < pys ? byk[(long long)(y0 + yy) * pys + i] : T(0);
+        }
+        __syncthreads();
+        if (active) {
+            for (int yy = 0; yy < yn; ++yy) {
+                const T tv = src[(long long)(y0 + yy) * ystride];
+                const T* b = sby + yy * PYT;
+#pragma unroll
+                for (int i = 0; i < PYT; ++i) acc[i] = fma(b[i], tv, acc[i]);
+            }
+        }
+    }
+    if (active) {
+        T* so = sout + (size_t)pl * PYT * Px;
+#pragma unroll
+        for (int i = 0; i < PYT; ++i) so[i * Px + jx] = acc[i];
+    }
+    __syncthreads();
+    for (int pp = 0; pp < ppc; ++pp) {
+        const long long pr = (long long)blockIdx.x * ppc + pp;
+        if (pr >= npairs) break;
+        const T* so = sout + (size_t)pp * PYT * Px;
+        for (int j = tid; j < L; j += blockDim.x) out[pr * L + j] = so[m_ipy[j] * Px + m_jx[j]] * scale[j];
+    }
+}
+
+template <typename T, int PYT>
+cudaError_t launch_ypass_gemm(const zl_plan_s& p, const T* t1, int ldp, const T* byk, const int* m_ipy,
+                              const int* m_jx, const T* scale, T* out, int R, cudaStream_t s) {
+    const int npairs = R * p.d.K;
+    const int ppc = kThreads / p.Px;
+    const size_t smem = ((size_t)kYChunk * PYT + (size_t)ppc * PYT * p.Px) * sizeof(T);
+    cudaError_t e = cudaFuncSetAttribute(fwd_ypass_gemm<T, PYT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int grid = (npairs + ppc - 1) / ppc;
+    p.timer.begin(ZL_STAGE_FWD_YPASS, s);
+    fwd_ypass_gemm<T, PYT><<<grid, kThreads, smem, s>>>(t1, byk, m_ipy, m_jx, scale, out, npairs, ppc, p.d.ny, p.Px,
+                                                         ldp, p.L, p.pys);
+    p.timer.end(s);
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_ypass(const zl_plan_s& p, const T* t1, int ldp, const T* by, const int* m_py, const int* m_jx,
-                         const T* scale, T* out, int R, cudaStream_t s) {
+                         const T* scale, T* out, int R, cudaStream_t s, const Tables<T>* tb = nullptr) {
     const int ny = p.d.ny, K = p.d.K;
+    if (tb != nullptr && p.Px <= kThreads) {
+        if (p.Py <= 16) return launch_ypass_gemm<T, 16>(p, t1, ldp, tb->byk, tb->m_ipy, m_jx, scale, out, R, s);
+        if (p.Py <= 32) return launch_ypass_gemm<T, 32>(p, t1, ldp, tb->byk, tb->m_ipy, m_jx, scale, out, R, s);
+        if (p.Py <= 48) return launch_ypass_gemm<T, 48>(p, t1, ldp, tb->byk, tb->m_ipy, m_jx, scale, out, R, s);
+        if (p.Py <= 64) return launch_ypass_gemm<T, 64>(p, t1, ldp, tb->byk, tb->m_ipy, m_jx, scale, out, R, s);
+    }
     int ychunk = ny;
     while ((size_t)(p.L + p.Px * (ychunk + 1)) * sizeof(T) > 96 * 1024 && ychunk > 1) ychunk = (ychunk + 1) / 2;
     const size_t smem = (size_t)(p.L + p.Px * (ychunk + 1)) * sizeof(T);
     cudaError_t e = cudaFuncSetAttribute(fwd_ypass<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     p.timer.begin(ZL_STAGE_FWD_YPASS, s);
-    fwd_ypass<T><<<dim3(K, R), kThreads, smem, s>>>(t1, by, m_py, m_jx, scale, out, K, ny, p.Px, ldp, p.L, ychunk);
+    fwd_ypass<T><<<dim3(K, R), kThreads, smem, s>>>(t1, by, m_py, m_jx, scale, out, R, K, ny, p.Px, ldp, p.L, ychunk);
     p.timer.end(s);
     return cudaGetLastError();
 }
@@ -261,13 +340,13 @@ cudaError_t launch_ypass(const zl_plan_s& p, const T* t1, int ldp, const T* by, 
 
 cudaError_t forward_ypass_f32(const zl_plan_s& p, const float* t1, int ldp, const float* scale, float* out, int R,
                               cudaStream_t s) {
-    return launch_ypass<float>(p, t1, ldp, p.tf.by, p.tf.m_py, p.tf.m_jx, scale, out, R, s);
+    return launch_ypass<float>(p, t1, ldp, p.tf.by, p.tf.m_py, p.tf.m_jx, scale, out, R, s, &p.tf);
 }
 
 template <typename T>
 cudaError_t forward_plain(const zl_plan_s& p, const Tables<T>& t, const T* M, const T* scale, const T* x, T* out,
                           int R, cudaStream_t s) {
-    const int nx = p.d.nx, ny = p.d.ny, K = p.d.K;
+    const int nx = p.d.nx;
     T* t1 = reinterpret_cast<T*>(p.t1);
     cudaError_t e;
     const size_t row = (size_t)KC * (nx + 1) * sizeof(T);
@@ -279,7 +358,7 @@ cudaError_t forward_plain(const zl_plan_s& p, const Tables<T>& t, const T* M, co
     p.timer.end(s);
     if (e != cudaSuccess) return e;
 
-    return launch_ypass<T>(p, t1, p.Px, t.by, t.m_py, t.m_jx, scale, out, R, s);
+    return launch_ypass<T>(p, t1, p.Px, t.by, t.m_py, t.m_jx, scale, out, R, s, &t);
 }
 
 template <typename T>

@@ -7,22 +7,27 @@
 // runs on the tensor cores with FP16 operand splits P = P_hi + P_lo and
 // x = x_hi + x_lo: the A operand stacks [P_hi; P_lo] (M = 128 rows = 2 x 64
 // members), so two MMAs (B = x_hi, then B = x_lo) leave all four partial
-// products in TMEM (rows k: P_hi x, rows 64 + k: P_lo x).  The epilogue warps
-// add the two halves, split the FP32 sum into FP16 hi/lo again and write it as
-// the A operand of the x-pass, whose rows are the (rhs, member) pairs of the
-// unit and whose K dimension runs along the grid row.  The x-pass MMA
-// multiplies by the pruned real-Fourier basis of the row (N = 48 >= Px kept
-// x-frequencies, hi/lo split, three products) and accumulates the whole row in
-// TMEM.  The regrouping of w^(m) into member segments (steps V2-V3, the
+// products in TMEM (lanes k: P_hi x, lanes 64 + k: P_lo x).  The epilogue warps
+// split each half into FP16 hi/lo again and write it as the A operand W of the
+// x-pass, whose rows are the (rhs, member) pairs of the unit and whose K
+// dimension runs along the grid row: one K-step per 8-column group, K-chunk 0
+// holding the P_hi x half and K-chunk 1 the P_lo x half of the same 8 columns,
+// so the x-pass MMA itself adds the two halves (its basis operand repeats the
+// 8 columns' basis values in both chunks).  The x-pass multiplies by the pruned
+// real-Fourier basis of the row (N = 48 >= Px kept x-frequencies, hi/lo split,
+// three products) and accumulates the whole row in TMEM.  The regrouping of w^(m) into member segments (steps V2-V3, the
 // paper's inter-processor exchange) thus never leaves the SM.  The y-pass,
 // Delta^{-1/2} scaling and compaction (the rest of V4, and V5) follow in the
 // CUDA-core kernel fwd_ypass.
 //
-// Warp roles (192 threads): warp 0 lane 0 = TMA producer (x tiles through a
-// 3-D tensor map, the per-column [P_hi; P_lo] images by 1-D bulk copies),
-// warp 1 = TMEM allocator + single-thread MMA issuer, warps 2-5 = converters
-// (x tile -> FP16 hi/lo B operand) and epilogue (TMEM -> W operand, TMEM ->
-// intermediate t1).  All waits are bounded; on timeout the kernel records an
+// Warp roles (320 threads): warp 0 lane 0 = TMA producer (x tiles through a
+// 3-D tensor map; the per-column [P_hi; P_lo] images and the per-group x-pass
+// basis by 1-D bulk copies), warp 1 = TMEM allocator + single-thread MMA
+// issuer, warps 2-9 = converters (x tile -> FP16 hi/lo B operand, two groups
+// ahead) and epilogue (TMEM -> W operand; TMEM -> intermediate t1
+// [ny][R][K][pxp]); two epilogue warps share each TMEM lane quarter and split
+// the unit's right-hand sides.  The MMA issue order V1(g), x-pass(g-1) keeps the
+// tensor pipe busy while the epilogue turns D1(g) into W(g).  All waits are bounded; on timeout the kernel records an
 // error code, drains its own copies, frees TMEM and returns.
 
 #include "zl_internal.cuh"
@@ -38,7 +43,7 @@ namespace zl {
 
 struct TcOperands {
     __half* pimg = nullptr;    // [nh][128 rows][nwp] K-major image of [P_hi; P_lo] per column
-    __half* bximg = nullptr;   // [2 splits][nx/8 chunks][6 row groups][8][8] x-pass basis image
+    uint8_t* bximg = nullptr;  // per 8-column group: [2 splits][2 chunks (same values)][6 row groups][128 B]
     int* d_err = nullptr;      // device error word (0 = ok)
     int nwp = 0;               // V1 K extent: n_w rounded up to 16 or 32
     int pxp = 0;               // row stride of t1 (Px rounded up to 4)
@@ -51,40 +56,42 @@ namespace {
 using namespace tc;
 
 constexpr int RC = 16;                 // right-hand sides per unit (V1 N)
-constexpr int GC = 8;                  // columns per gather group (one K-chunk of the x-pass)
+constexpr int GC = 8;                  // columns per group (one x-pass K-step: 8 columns x 2 halves)
 constexpr int N2 = 48;                 // x-pass N: kept x-frequencies padded
 constexpr int MT = 8;                  // x-pass M tiles: 64 members x 16 rhs / 128
-constexpr int SP = 4;                  // P image ring depth
+constexpr int SP = 8;                  // P image ring depth (one group)
 constexpr int SX = 2;                  // x tile ring depth
-constexpr int kThreadsTc = 192;
+constexpr int SB = 2;                  // x-pass basis ring depth
+constexpr int NEPI = 8;                // epilogue / converter warps
+constexpr int kThreadsTc = 64 + 32 * NEPI;
+constexpr int kEpiThreads = 32 * NEPI;
 constexpr uint32_t kD1Col = MT * N2;   // 384: D1 (V1 accumulators) after the x-pass accumulators
 constexpr uint32_t kTmemCols = 512;
-constexpr uint32_t kWChunk = 16384;    // one 8-column K-chunk of W: 1024 rows x 16 B
+constexpr uint32_t kWChunk = 16384;    // one K-chunk of W: 1024 rows x 16 B
 constexpr uint32_t kWSplit = 32768;    // hi / lo offset inside W
+constexpr uint32_t kBxStage = 3072;    // x-pass basis per group: 2 splits x 2 chunks x 6 row groups x 128 B
 constexpr unsigned long long kWaitCycles = 4000000000ull;   // ~2 s at 2 GHz
 
 struct SmemPlan {
-    uint32_t bx, pring, xring, b1, w, scratch, bars, total;
+    uint32_t pring, xring, bxring, b1, w, bars, total;
 };
 
 __host__ __device__ inline uint32_t b1_stride(int nwp) { return 64u * nwp + 16u; }   // hi + lo + 16 B pad
 
-__host__ __device__ inline SmemPlan smem_plan(int nx, int nwp) {
+__host__ __device__ inline SmemPlan smem_plan(int nwp) {
     SmemPlan s;
     uint32_t o = 0;
-    s.bx = o;
-    o += 2u * nx * 96u;                  // 2 splits x nx/8 chunks x 6 row groups x 128 B
     s.pring = o;
     o += SP * 256u * nwp;                // 128 rows x nwp x 2 B
     s.xring = o;
     o += SX * 512u * nwp;                // RC x nwp x GC x 4 B
+    s.bxring = o;
+    o += SB * kBxStage;
     s.b1 = o;
-    o += GC * b1_stride(nwp);
+    o += 2 * GC * b1_stride(nwp);
     o = (o + 127u) & ~127u;
     s.w = o;
     o += 2 * kWSplit;
-    s.scratch = o;
-    o += 16384;
     s.bars = o;
     o += 256;
     s.total = o;
@@ -97,16 +104,16 @@ enum {
     B_PEMPTY = B_PFULL + SP,
     B_XFULL = B_PEMPTY + SP,
     B_XEMPTY = B_XFULL + SX,
-    B_B1FULL = B_XEMPTY + SX,
-    B_B1EMPTY,
-    B_D1FULL,
+    B_BXFULL = B_XEMPTY + SX,
+    B_BXEMPTY = B_BXFULL + SB,
+    B_B1FULL = B_BXEMPTY + SB,
+    B_B1EMPTY = B_B1FULL + 2,
+    B_D1FULL = B_B1EMPTY + 2,
     B_D1EMPTY,
     B_WFULL,
     B_WEMPTY,
     B_D2FULL,
     B_D2EMPTY,
-    B_EX0,
-    B_EX1,
     B_FIN,
     B_COUNT
 };
@@ -141,29 +148,40 @@ __device__ __forceinline__ void split2(float a, float b, uint32_t& hi, uint32_t&
     lo = *reinterpret_cast<const uint32_t*>(&l);
 }
 
+// Bounded drain of a producer ring slot: wait for the last phase issued into it.
+__device__ __forceinline__ void drain_slot(uint64_t* bar, uint32_t issued, uint32_t slot, uint32_t depth) {
+    if (issued <= slot) return;
+    const uint32_t n = (issued - slot + depth - 1) / depth;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, (n - 1) & 1u) && (unsigned long long)(clock64() - t0) < kWaitCycles) {}
+}
+
 __global__ void __launch_bounds__(kThreadsTc, 1)
 fwd_column_tc_kernel(const __grid_constant__ CUtensorMap tmap_x, const __half* __restrict__ pimg,
-                     const __half* __restrict__ bximg, float* __restrict__ t1, int* __restrict__ err,
-                     int R, int K, int nx, int ny, int nwp, int Px, int pxp) {
+                     const uint8_t* __restrict__ bximg, float* __restrict__ t1, int* __restrict__ err,
+                     int R, int K, int nx, int ny, int nwp, int pxp) {
     extern __shared__ __align__(1024) uint8_t smem[];
-    const SmemPlan sp = smem_plan(nx, nwp);
+    const SmemPlan sp = smem_plan(nwp);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + sp.bars);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + B_COUNT);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
-    uint8_t* sbx = smem + sp.bx;
     uint8_t* spring = smem + sp.pring;
     uint8_t* sxring = smem + sp.xring;
+    uint8_t* sbxring = smem + sp.bxring;
     uint8_t* sb1 = smem + sp.b1;
     uint8_t* sw = smem + sp.w;
-    float4* sscr = reinterpret_cast<float4*>(smem + sp.scratch);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int n_rc = (R + RC - 1) / RC;
     const int units = ny * n_rc;
     const int G = nx / GC;
+    // units of this CTA: blockIdx.x + i * gridDim.x; groups are numbered across them
+    const int my_units = blockIdx.x < units ? (units - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const uint32_t total_groups = (uint32_t)my_units * (uint32_t)G;
     const uint32_t PBYTES = 256u * nwp;
     const uint32_t XBYTES = 512u * nwp;
     const uint32_t B1S = b1_stride(nwp);
+    const uint32_t B1BUF = GC * B1S;
     const uint32_t b1_sbo = (uint32_t)(nwp / 8) * 128u;
 
     if (tid == 0) {
@@ -173,32 +191,28 @@ fwd_column_tc_kernel(const __grid_constant__ CUtensorMap tmap_x, const __half* _
         }
         for (int i = 0; i < SX; ++i) {
             mbar_init(&bars[B_XFULL + i], 1);
-            mbar_init(&bars[B_XEMPTY + i], 128);
+            mbar_init(&bars[B_XEMPTY + i], kEpiThreads);
         }
-        mbar_init(&bars[B_B1FULL], 128);
-        mbar_init(&bars[B_B1EMPTY], 1);
+        for (int i = 0; i < SB; ++i) {
+            mbar_init(&bars[B_BXFULL + i], 1);
+            mbar_init(&bars[B_BXEMPTY + i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&bars[B_B1FULL + i], kEpiThreads);
+            mbar_init(&bars[B_B1EMPTY + i], 1);
+        }
         mbar_init(&bars[B_D1FULL], 1);
-        mbar_init(&bars[B_D1EMPTY], 128);
-        mbar_init(&bars[B_WFULL], 128);
+        mbar_init(&bars[B_D1EMPTY], kEpiThreads);
+        mbar_init(&bars[B_WFULL], kEpiThreads);
         mbar_init(&bars[B_WEMPTY], 1);
         mbar_init(&bars[B_D2FULL], 1);
-        mbar_init(&bars[B_D2EMPTY], 128);
-        mbar_init(&bars[B_EX0], 128);
-        mbar_init(&bars[B_EX1], 128);
+        mbar_init(&bars[B_D2EMPTY], kEpiThreads);
         mbar_init(&bars[B_FIN], 1);
         *abort_flag = 0;
         fence_mbar_init();
         prefetch_tmap(&tmap_x);
     }
     if (warp == 1) tmem_alloc(tslot, kTmemCols);
-    // the x-pass basis image is the same for every row: load it once
-    {
-        const int4* src = reinterpret_cast<const int4*>(bximg);
-        int4* dst = reinterpret_cast<int4*>(sbx);
-        const int n16 = (int)(2u * nx * 96u / 16u);
-        for (int i = tid; i < n16; i += blockDim.x) dst[i] = src[i];
-        fence_proxy_async_smem();
-    }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -207,43 +221,35 @@ fwd_column_tc_kernel(const __grid_constant__ CUtensorMap tmap_x, const __half* _
     if (warp == 0) {
         // ------------------------------------------------------------ producer
         if (lane == 0) {
-            uint32_t pc = 0, xc = 0;
+            uint32_t pc = 0, xc = 0, bc = 0;
             bool ok = true;
-            for (int u = blockIdx.x; u < units && ok; u += gridDim.x) {
+            for (uint32_t gi = 0; gi < total_groups && ok; ++gi) {
+                const int u = (int)blockIdx.x + (int)(gi / G) * (int)gridDim.x;
+                const int g = (int)(gi % G);
                 const int y = u / n_rc, r0 = (u % n_rc) * RC;
-                for (int g = 0; g < G && ok; ++g) {
-                    const uint32_t xs = xc % SX, xph = (xc / SX) & 1u;
-                    if (!wait_bar(&bars[B_XEMPTY + xs], xph ^ 1u, abort_flag)) { fail(abort_flag, err, 1); ok = false; break; }
-                    mbar_arrive_expect_tx(&bars[B_XFULL + xs], XBYTES);
-                    tma_load_3d(sxring + xs * XBYTES, &tmap_x, y * nx + g * GC, 0, r0, &bars[B_XFULL + xs]);
-                    ++xc;
-                    for (int j = 0; j < GC; ++j) {
-                        const uint32_t ps = pc % SP, pph = (pc / SP) & 1u;
-                        if (!wait_bar(&bars[B_PEMPTY + ps], pph ^ 1u, abort_flag)) { fail(abort_flag, err, 1); ok = false; break; }
-                        mbar_arrive_expect_tx(&bars[B_PFULL + ps], PBYTES);
-                        const size_t col = (size_t)y * nx + (size_t)g * GC + j;
-                        bulk_g2s(spring + ps * PBYTES, pimg + col * 128u * nwp, PBYTES, &bars[B_PFULL + ps]);
-                        ++pc;
-                    }
+                const uint32_t xs = xc % SX, xph = (xc / SX) & 1u;
+                if (!wait_bar(&bars[B_XEMPTY + xs], xph ^ 1u, abort_flag)) { fail(abort_flag, err, 1); ok = false; break; }
+                mbar_arrive_expect_tx(&bars[B_XFULL + xs], XBYTES);
+                tma_load_3d(sxring + xs * XBYTES, &tmap_x, y * nx + g * GC, 0, r0, &bars[B_XFULL + xs]);
+                ++xc;
+                const uint32_t bs = bc % SB, bph = (bc / SB) & 1u;
+                if (!wait_bar(&bars[B_BXEMPTY + bs], bph ^ 1u, abort_flag)) { fail(abort_flag, err, 1); ok = false; break; }
+                mbar_arrive_expect_tx(&bars[B_BXFULL + bs], kBxStage);
+                bulk_g2s(sbxring + bs * kBxStage, bximg + (size_t)g * kBxStage, kBxStage, &bars[B_BXFULL + bs]);
+                ++bc;
+                for (int j = 0; j < GC; ++j) {
+                    const uint32_t ps = pc % SP, pph = (pc / SP) & 1u;
+                    if (!wait_bar(&bars[B_PEMPTY + ps], pph ^ 1u, abort_flag)) { fail(abort_flag, err, 1); ok = false; break; }
+                    mbar_arrive_expect_tx(&bars[B_PFULL + ps], PBYTES);
+                    const size_t col = (size_t)y * nx + (size_t)g * GC + j;
+                    bulk_g2s(spring + ps * PBYTES, pimg + col * 128u * nwp, PBYTES, &bars[B_PFULL + ps]);
+                    ++pc;
                 }
             }
-            // drain: every issued copy must land before the CTA exits
-            for (uint32_t s = 0; s < SP; ++s) {
-                if (pc > s) {
-                    const uint32_t nissued = (pc - s + SP - 1) / SP;   // loads issued into slot s
-                    const uint32_t par = (nissued - 1) & 1u;
-                    const long long t0 = clock64();
-                    while (!mbar_try_wait(&bars[B_PFULL + s], par) && (unsigned long long)(clock64() - t0) < kWaitCycles) {}
-                }
-            }
-            for (uint32_t s = 0; s < SX; ++s) {
-                if (xc > s) {
-                    const uint32_t nissued = (xc - s + SX - 1) / SX;
-                    const uint32_t par = (nissued - 1) & 1u;
-                    const long long t0 = clock64();
-                    while (!mbar_try_wait(&bars[B_XFULL + s], par) && (unsigned long long)(clock64() - t0) < kWaitCycles) {}
-                }
-            }
+            // every issued copy must land before the CTA exits
+            for (uint32_t s = 0; s < SP; ++s) drain_slot(&bars[B_PFULL + s], pc, s, SP);
+            for (uint32_t s = 0; s < SX; ++s) drain_slot(&bars[B_XFULL + s], xc, s, SX);
+            for (uint32_t s = 0; s < SB; ++s) drain_slot(&bars[B_BXFULL + s], bc, s, SB);
         }
     } else if (warp == 1) {
         // ------------------------------------------------------------ MMA issuer
@@ -251,83 +257,83 @@ fwd_column_tc_kernel(const __grid_constant__ CUtensorMap tmap_x, const __half* _
             const uint32_t idesc_v1 = idesc_f16_f32(128, RC);
             const uint32_t idesc_x = idesc_f16_f32(128, N2);
             const uint32_t a_sbo = (uint32_t)(nwp / 8) * 128u;
-            const uint32_t bx_lbo = 6u * 128u;
-            const uint32_t bx_split = (uint32_t)(nx / 8) * bx_lbo;
-            uint32_t pc = 0, gc = 0, kc = 0, uc = 0;
+            uint32_t pc = 0;
             bool ok = true;
-            for (int u = blockIdx.x; u < units && ok; u += gridDim.x) {
-                for (int g = 0; g < G && ok; ++g) {
-                    if (!wait_bar(&bars[B_B1FULL], gc & 1u, abort_flag) ||
-                        !wait_bar(&bars[B_D1EMPTY], (gc & 1u) ^ 1u, abort_flag)) { fail(abort_flag, err, 2); ok = false; break; }
+            // x-pass of group gi (W and basis stage of gi ready); first of a unit overwrites D2
+            auto xpass = [&](uint32_t gi) -> bool {
+                const uint32_t bs = gi % SB, bph = (gi / SB) & 1u;
+                if (!wait_bar(&bars[B_WFULL], gi & 1u, abort_flag)) return false;
+                if (!wait_bar(&bars[B_BXFULL + bs], bph, abort_flag)) return false;
+                const bool first = (gi % G) == 0;
+                if (first && !wait_bar(&bars[B_D2EMPTY], ((gi / G) & 1u) ^ 1u, abort_flag)) return false;
+                tc_fence_after();
+                const uint32_t bhi = smem_u32(sbxring + bs * kBxStage), blo = bhi + kBxStage / 2;
+                const uint64_t dbhi = smem_desc(bhi, 768u, 128u), dblo = smem_desc(blo, 768u, 128u);
+                for (int t = 0; t < MT; ++t) {
+                    const uint32_t ahi = smem_u32(sw) + (uint32_t)t * 2048u;
+                    const uint64_t dahi = smem_desc(ahi, kWChunk, 128u), dalo = smem_desc(ahi + kWSplit, kWChunk, 128u);
+                    const uint32_t d = tbase + (uint32_t)t * N2;
+                    mma_f16(d, dahi, dbhi, idesc_x, first ? 0u : 1u);
+                    mma_f16(d, dalo, dbhi, idesc_x, 1u);
+                    mma_f16(d, dahi, dblo, idesc_x, 1u);
+                }
+                mma_commit(&bars[B_WEMPTY]);
+                mma_commit(&bars[B_BXEMPTY + bs]);
+                if ((gi % G) == (uint32_t)G - 1) mma_commit(&bars[B_D2FULL]);
+                return true;
+            };
+            for (uint32_t gi = 0; gi < total_groups && ok; ++gi) {
+                const uint32_t b = gi & 1u, n = gi >> 1;
+                if (!wait_bar(&bars[B_B1FULL + b], n & 1u, abort_flag) ||
+                    !wait_bar(&bars[B_D1EMPTY], (gi & 1u) ^ 1u, abort_flag)) { fail(abort_flag, err, 2); ok = false; break; }
+                tc_fence_after();
+                for (int j = 0; j < GC; ++j) {
+                    const uint32_t ps = pc % SP, pph = (pc / SP) & 1u;
+                    if (!wait_bar(&bars[B_PFULL + ps], pph, abort_flag)) { fail(abort_flag, err, 2); ok = false; break; }
                     tc_fence_after();
-                    for (int j = 0; j < GC; ++j) {
-                        const uint32_t ps = pc % SP, pph = (pc / SP) & 1u;
-                        if (!wait_bar(&bars[B_PFULL + ps], pph, abort_flag)) { fail(abort_flag, err, 2); ok = false; break; }
-                        tc_fence_after();
-                        const uint32_t a0 = smem_u32(spring + ps * PBYTES);
-                        const uint32_t bhi = smem_u32(sb1 + j * B1S);
-                        const uint32_t blo = bhi + 32u * nwp;
-                        const uint32_t d = tbase + kD1Col + (uint32_t)j * RC;
-                        for (int ks = 0; ks < nwp / 16; ++ks)
-                            mma_f16(d, smem_desc(a0 + ks * 256u, 128u, a_sbo), smem_desc(bhi + ks * 256u, 128u, b1_sbo),
-                                    idesc_v1, ks > 0);
-                        for (int ks = 0; ks < nwp / 16; ++ks)
-                            mma_f16(d, smem_desc(a0 + ks * 256u, 128u, a_sbo), smem_desc(blo + ks * 256u, 128u, b1_sbo),
-                                    idesc_v1, 1u);
-                        mma_commit(&bars[B_PEMPTY + ps]);
-                        ++pc;
-                    }
-                    if (!ok) break;
-                    mma_commit(&bars[B_D1FULL]);
-                    mma_commit(&bars[B_B1EMPTY]);
-                    ++gc;
-                    if (g & 1) {
-                        const int s = g >> 1;
-                        if (!wait_bar(&bars[B_WFULL], kc & 1u, abort_flag)) { fail(abort_flag, err, 2); ok = false; break; }
-                        if (s == 0 && !wait_bar(&bars[B_D2EMPTY], (uc & 1u) ^ 1u, abort_flag)) { fail(abort_flag, err, 2); ok = false; break; }
-                        tc_fence_after();
-                        const uint32_t bhi = smem_u32(sbx) + (uint32_t)s * 2u * bx_lbo;
-                        const uint32_t blo = bhi + bx_split;
-                        const uint64_t dbhi = smem_desc(bhi, bx_lbo, 128u), dblo = smem_desc(blo, bx_lbo, 128u);
-                        for (int t = 0; t < MT; ++t) {
-                            const uint32_t ahi = smem_u32(sw) + (uint32_t)t * 2048u;
-                            const uint64_t dahi = smem_desc(ahi, kWChunk, 128u), dalo = smem_desc(ahi + kWSplit, kWChunk, 128u);
-                            const uint32_t d = tbase + (uint32_t)t * N2;
-                            mma_f16(d, dahi, dbhi, idesc_x, s > 0);
-                            mma_f16(d, dalo, dbhi, idesc_x, 1u);
-                            mma_f16(d, dahi, dblo, idesc_x, 1u);
-                        }
-                        mma_commit(&bars[B_WEMPTY]);
-                        ++kc;
-                    }
+                    const uint32_t a0 = smem_u32(spring + ps * PBYTES);
+                    const uint32_t bhi = smem_u32(sb1 + b * B1BUF + j * B1S);
+                    const uint32_t blo = bhi + 32u * nwp;
+                    const uint32_t d = tbase + kD1Col + (uint32_t)j * RC;
+                    for (int ks = 0; ks < nwp / 16; ++ks)
+                        mma_f16(d, smem_desc(a0 + ks * 256u, 128u, a_sbo), smem_desc(bhi + ks * 256u, 128u, b1_sbo),
+                                idesc_v1, ks > 0);
+                    for (int ks = 0; ks < nwp / 16; ++ks)
+                        mma_f16(d, smem_desc(a0 + ks * 256u, 128u, a_sbo), smem_desc(blo + ks * 256u, 128u, b1_sbo),
+                                idesc_v1, 1u);
+                    mma_commit(&bars[B_PEMPTY + ps]);
+                    ++pc;
                 }
                 if (!ok) break;
-                mma_commit(&bars[B_D2FULL]);
-                ++uc;
+                mma_commit(&bars[B_D1FULL]);
+                mma_commit(&bars[B_B1EMPTY + b]);
+                if (gi > 0 && !xpass(gi - 1)) { fail(abort_flag, err, 2); ok = false; break; }
             }
+            if (ok && total_groups > 0 && !xpass(total_groups - 1)) fail(abort_flag, err, 2);
             mma_commit(&bars[B_FIN]);
             const long long t0 = clock64();
             while (!mbar_try_wait(&bars[B_FIN], 0) && (unsigned long long)(clock64() - t0) < kWaitCycles) {}
         }
     } else {
         // ------------------------------------------------------------ converters + epilogue
-        const int et = tid - 64;                 // 0..127
-        const int q = warp & 3;                  // TMEM lane quarter this warp may access
+        const int et = tid - 64;                       // 0 .. kEpiThreads-1
+        const int q = warp & 3;                        // TMEM lane quarter this warp may access
+        const int rset = (warp - 2) >> 2;              // rhs half of the unit this warp finalises
         const uint32_t lane_off = (uint32_t)(32 * q) << 16;
-        const bool top = q < 2;                  // lanes 0-63: P_hi x;  lanes 64-127: P_lo x
-        const int kk = (q & 1) * 32 + lane;      // member of this thread's TMEM lane
-        const int my_r0 = top ? 0 : 8, other_r0 = top ? 8 : 0;
-        const int region = q & 1;
-        uint32_t xc = 0, cc = 0, gc = 0, kc = 0, uc = 0, exc = 0;
+        const int kk = (q & 1) * 32 + lane;            // member of this thread's TMEM lane
+        const uint32_t half_chunk = q < 2 ? 0u : kWChunk;   // P_hi x -> K-chunk 0, P_lo x -> K-chunk 1
+        uint32_t conv = 0;
         bool ok = true;
 
-        auto convert = [&](int) -> bool {
-            const uint32_t xs = xc % SX, xph = (xc / SX) & 1u;
+        auto convert = [&](uint32_t c) -> bool {
+            const uint32_t xs = c % SX, xph = (c / SX) & 1u;
+            const uint32_t b = c & 1u, n = c >> 1;
             if (!warp_wait_bar(&bars[B_XFULL + xs], xph, abort_flag)) return false;
-            if (!warp_wait_bar(&bars[B_B1EMPTY], (cc & 1u) ^ 1u, abort_flag)) return false;
-            const float* xt = reinterpret_cast<const float*>(sxring + xs * XBYTES);   // [r][l][m] = [RC][nwp][GC]
+            if (!warp_wait_bar(&bars[B_B1EMPTY + b], (n & 1u) ^ 1u, abort_flag)) return false;
+            const float* xt = reinterpret_cast<const float*>(sxring + xs * XBYTES);   // [RC][nwp][GC]
+            uint8_t* b1 = sb1 + b * B1BUF;
             const int noct = nwp / 8;
-            for (int item = et; item < GC * RC * noct; item += 128) {
+            for (int item = et; item < GC * RC * noct; item += kEpiThreads) {
                 const int j = item % GC, rest = item / GC;
                 const int o = rest % noct, r = rest / noct;
                 float v[8];
@@ -338,112 +344,82 @@ fwd_column_tc_kernel(const __grid_constant__ CUtensorMap tmap_x, const __half* _
                 split2(v[2], v[3], hi.y, lo.y);
                 split2(v[4], v[5], hi.z, lo.z);
                 split2(v[6], v[7], hi.w, lo.w);
-                uint8_t* dst = sb1 + j * B1S + (r >> 3) * b1_sbo + o * 128u + (r & 7) * 16u;
+                uint8_t* dst = b1 + j * B1S + (r >> 3) * b1_sbo + o * 128u + (r & 7) * 16u;
                 *reinterpret_cast<uint4*>(dst) = hi;
                 *reinterpret_cast<uint4*>(dst + 32u * nwp) = lo;
             }
             fence_proxy_async_smem();
-            mbar_arrive(&bars[B_B1FULL]);
+            mbar_arrive(&bars[B_B1FULL + b]);
             mbar_arrive(&bars[B_XEMPTY + xs]);
-            ++xc;
-            ++cc;
             return true;
         };
 
-        for (int u = blockIdx.x; u < units && ok; u += gridDim.x) {
+        while (conv < total_groups && conv < 2) {
+            if (!convert(conv)) { fail(abort_flag, err, 3); ok = false; break; }
+            ++conv;
+        }
+        for (uint32_t gi = 0; gi < total_groups && ok; ++gi) {
+            const int u = (int)blockIdx.x + (int)(gi / G) * (int)gridDim.x;
             const int y = u / n_rc, r0 = (u % n_rc) * RC;
-            if (!convert(0)) { fail(abort_flag, err, 3); ok = false; break; }
-            for (int g = 0; g < G && ok; ++g) {
-                if (g + 1 < G && !convert(g + 1)) { fail(abort_flag, err, 3); ok = false; break; }
-                // ---- drain D1 of group g: exchange halves, sum, split, write W
-                if (!warp_wait_bar(&bars[B_D1FULL], gc & 1u, abort_flag)) { fail(abort_flag, err, 3); ok = false; break; }
-                tc_fence_after();
-                float acc[GC][8];
-#pragma unroll
-                for (int pass = 0; pass < 2; ++pass) {
-                    if (!ok) break;
-#pragma unroll
-                    for (int jj = 0; jj < 4; ++jj) {
-                        const int j = 4 * pass + jj;
-                        uint32_t v[8];
-                        tmem_ld8(tbase + lane_off + kD1Col + (uint32_t)(j * RC + other_r0), v);
-                        tmem_ld_wait();
-                        float4* slot = sscr + ((((region * 2 + (top ? 0 : 1)) * 4 + jj) * 2) * 32);
-                        slot[lane] = make_float4(__uint_as_float(v[0]), __uint_as_float(v[1]), __uint_as_float(v[2]), __uint_as_float(v[3]));
-                        slot[32 + lane] = make_float4(__uint_as_float(v[4]), __uint_as_float(v[5]), __uint_as_float(v[6]), __uint_as_float(v[7]));
-                    }
-                    mbar_arrive(&bars[B_EX0]);
-                    if (!warp_wait_bar(&bars[B_EX0], exc & 1u, abort_flag)) { fail(abort_flag, err, 3); ok = false; break; }
-#pragma unroll
-                    for (int jj = 0; jj < 4; ++jj) {
-                        const int j = 4 * pass + jj;
-                        uint32_t v[8];
-                        tmem_ld8(tbase + lane_off + kD1Col + (uint32_t)(j * RC + my_r0), v);
-                        tmem_ld_wait();
-                        const float4* slot = sscr + ((((region * 2 + (top ? 1 : 0)) * 4 + jj) * 2) * 32);
-                        const float4 a = slot[lane], b = slot[32 + lane];
-                        acc[j][0] = __uint_as_float(v[0]) + a.x;
-                        acc[j][1] = __uint_as_float(v[1]) + a.y;
-                        acc[j][2] = __uint_as_float(v[2]) + a.z;
-                        acc[j][3] = __uint_as_float(v[3]) + a.w;
-                        acc[j][4] = __uint_as_float(v[4]) + b.x;
-                        acc[j][5] = __uint_as_float(v[5]) + b.y;
-                        acc[j][6] = __uint_as_float(v[6]) + b.z;
-                        acc[j][7] = __uint_as_float(v[7]) + b.w;
-                    }
-                    mbar_arrive(&bars[B_EX1]);
-                    if (!warp_wait_bar(&bars[B_EX1], exc & 1u, abort_flag)) { fail(abort_flag, err, 3); ok = false; break; }
-                    ++exc;
-                }
-                if (!ok) break;
-                tc_fence_before();
-                mbar_arrive(&bars[B_D1EMPTY]);
-                ++gc;
-                const int chunk = g & 1;
-                if (chunk == 0 && !warp_wait_bar(&bars[B_WEMPTY], (kc & 1u) ^ 1u, abort_flag)) { fail(abort_flag, err, 3); ok = false; break; }
-#pragma unroll
-                for (int rl = 0; rl < 8; ++rl) {
-                    const int r = my_r0 + rl;
-                    uint4 hi, lo;
-                    split2(acc[0][rl], acc[1][rl], hi.x, lo.x);
-                    split2(acc[2][rl], acc[3][rl], hi.y, lo.y);
-                    split2(acc[4][rl], acc[5][rl], hi.z, lo.z);
-                    split2(acc[6][rl], acc[7][rl], hi.w, lo.w);
-                    const uint32_t row = (uint32_t)r * 64u + (uint32_t)kk;
-                    const uint32_t off = (uint32_t)chunk * kWChunk + (row >> 3) * 128u + (row & 7u) * 16u;
-                    *reinterpret_cast<uint4*>(sw + off) = hi;
-                    *reinterpret_cast<uint4*>(sw + kWSplit + off) = lo;
-                }
-                fence_proxy_async_smem();
-                if (chunk == 1) {
-                    mbar_arrive(&bars[B_WFULL]);
-                    ++kc;
-                }
-            }
-            if (!ok) break;
-            // ---- drain D2: the row's x-pass, rows (r, k) -> t1[r0 + r][k][y][0..pxp)
-            if (!warp_wait_bar(&bars[B_D2FULL], uc & 1u, abort_flag)) { fail(abort_flag, err, 3); ok = false; break; }
+            // ---- D1 of group gi: 8 columns x 8 rhs of this thread's lane
+            if (!warp_wait_bar(&bars[B_D1FULL], gi & 1u, abort_flag)) { fail(abort_flag, err, 3); ok = false; break; }
             tc_fence_after();
-            for (int t = 0; t < MT; ++t) {
-                const int row = 128 * t + 32 * q + lane;
-                const int r = row >> 6, k = row & 63;
-                uint32_t v[16 * 3];
-                tmem_ld16(tbase + lane_off + (uint32_t)(t * N2), *reinterpret_cast<uint32_t(*)[16]>(&v[0]));
-                tmem_ld16(tbase + lane_off + (uint32_t)(t * N2 + 16), *reinterpret_cast<uint32_t(*)[16]>(&v[16]));
-                tmem_ld16(tbase + lane_off + (uint32_t)(t * N2 + 32), *reinterpret_cast<uint32_t(*)[16]>(&v[32]));
-                tmem_ld_wait();
-                if (r0 + r < R && k < K) {
-                    float4* dst = reinterpret_cast<float4*>(t1 + (((size_t)(r0 + r) * K + k) * ny + y) * pxp);
+            uint32_t v[GC][8];
 #pragma unroll
-                    for (int c = 0; c < N2 / 4; ++c)
-                        if (4 * c < pxp)
-                            dst[c] = make_float4(__uint_as_float(v[4 * c]), __uint_as_float(v[4 * c + 1]),
-                                                 __uint_as_float(v[4 * c + 2]), __uint_as_float(v[4 * c + 3]));
-                }
-            }
+            for (int j = 0; j < GC; ++j) tmem_ld8(tbase + lane_off + kD1Col + (uint32_t)(j * RC + rset * 8), v[j]);
+            tmem_ld_wait();
             tc_fence_before();
-            mbar_arrive(&bars[B_D2EMPTY]);
-            ++uc;
+            mbar_arrive(&bars[B_D1EMPTY]);
+            uint4 hi[8], lo[8];
+#pragma unroll
+            for (int rl = 0; rl < 8; ++rl) {
+                split2(__uint_as_float(v[0][rl]), __uint_as_float(v[1][rl]), hi[rl].x, lo[rl].x);
+                split2(__uint_as_float(v[2][rl]), __uint_as_float(v[3][rl]), hi[rl].y, lo[rl].y);
+                split2(__uint_as_float(v[4][rl]), __uint_as_float(v[5][rl]), hi[rl].z, lo[rl].z);
+                split2(__uint_as_float(v[6][rl]), __uint_as_float(v[7][rl]), hi[rl].w, lo[rl].w);
+            }
+            // ---- W: rows (r, k), K-chunk = half (P_hi x or P_lo x), 8 columns per 16-byte row
+            if (!warp_wait_bar(&bars[B_WEMPTY], (gi & 1u) ^ 1u, abort_flag)) { fail(abort_flag, err, 3); ok = false; break; }
+#pragma unroll
+            for (int rl = 0; rl < 8; ++rl) {
+                const uint32_t row = (uint32_t)(rset * 8 + rl) * 64u + (uint32_t)kk;
+                const uint32_t off = half_chunk + (row >> 3) * 128u + (row & 7u) * 16u;
+                *reinterpret_cast<uint4*>(sw + off) = hi[rl];
+                *reinterpret_cast<uint4*>(sw + kWSplit + off) = lo[rl];
+            }
+            fence_proxy_async_smem();
+            mbar_arrive(&bars[B_WFULL]);
+            // ---- keep the converters two groups ahead
+            if (conv < total_groups) {
+                if (!convert(conv)) { fail(abort_flag, err, 3); ok = false; break; }
+                ++conv;
+            }
+            // ---- end of a unit: D2 holds the row's x-pass, rows (r, k) -> t1[y][r0 + r][k][0..pxp)
+            if ((gi % G) == (uint32_t)G - 1) {
+                const uint32_t ui = gi / G;
+                if (!warp_wait_bar(&bars[B_D2FULL], ui & 1u, abort_flag)) { fail(abort_flag, err, 3); ok = false; break; }
+                tc_fence_after();
+#pragma unroll 1
+                for (int t = rset; t < MT; t += 2) {
+                    const int row = 128 * t + 32 * q + lane;
+                    const int r = row >> 6, k = row & 63;
+                    uint32_t dv[N2];
+                    tmem_ld16(tbase + lane_off + (uint32_t)(t * N2), *reinterpret_cast<uint32_t(*)[16]>(&dv[0]));
+                    tmem_ld16(tbase + lane_off + (uint32_t)(t * N2 + 16), *reinterpret_cast<uint32_t(*)[16]>(&dv[16]));
+                    tmem_ld16(tbase + lane_off + (uint32_t)(t * N2 + 32), *reinterpret_cast<uint32_t(*)[16]>(&dv[32]));
+                    tmem_ld_wait();
+                    if (r0 + r < R && k < K) {
+                        float4* dst = reinterpret_cast<float4*>(t1 + (((size_t)y * R + r0 + r) * K + k) * pxp);
+#pragma unroll
+                        for (int c = 0; c < N2 / 4; ++c)
+                            if (4 * c < pxp)
+                                dst[c] = make_float4(__uint_as_float(dv[4 * c]), __uint_as_float(dv[4 * c + 1]),
+                                                     __uint_as_float(dv[4 * c + 2]), __uint_as_float(dv[4 * c + 3]));
+                    }
+                }
+                tc_fence_before();
+                mbar_arrive(&bars[B_D2EMPTY]);
+            }
         }
     }
 
@@ -505,7 +481,7 @@ double basis_value_d(int N, int p, int m) {
 }  // namespace
 
 bool tc_supported(const zl_plan_s& p) {
-    return p.d.nx % 16 == 0 && p.d.nx <= 256 && p.d.K <= 64 && p.d.nw <= 32 && p.Px <= N2 && p.nh % 4 == 0;
+    return p.d.nx % GC == 0 && p.d.K <= 64 && p.d.nw <= 32 && p.Px <= N2 && p.nh % 4 == 0;
 }
 
 zl_status tc_prepare(zl_plan_s& p, cudaStream_t s) {
@@ -520,11 +496,11 @@ zl_status tc_prepare(zl_plan_s& p, cudaStream_t s) {
     t->nwp = p.d.nw <= 16 ? 16 : 32;
     t->pxp = (p.Px + 3) / 4 * 4;
     t->num_sms = sms;
-    t->smem = smem_plan(p.d.nx, t->nwp).total;
+    t->smem = smem_plan(t->nwp).total;
     const int nx = p.d.nx;
     cudaError_t e = cudaSuccess;
     const size_t pimg_bytes = (size_t)p.nh * 256u * t->nwp;
-    const size_t bx_bytes = 2u * nx * 96u;
+    const size_t bx_bytes = (size_t)(nx / GC) * kBxStage;
     e = cudaMalloc(&t->pimg, pimg_bytes);
     if (e == cudaSuccess) e = cudaMalloc(&t->bximg, bx_bytes);
     if (e == cudaSuccess) e = cudaMalloc(&t->d_err, sizeof(int));
@@ -535,17 +511,21 @@ zl_status tc_prepare(zl_plan_s& p, cudaStream_t s) {
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) {
-        // x-pass basis image: rows jx < Px hold b_{p_x}(x) of the kept x-frequencies
+        // x-pass basis image, one stage per 8-column group g: B[jx][(h, m)] = b_{p_x}(8g + m) for both
+        // halves h (the K-chunk h of W holds P_hi x for h = 0 and P_lo x for h = 1); rows jx >= Px are 0
         std::vector<__half> img(bx_bytes / 2, __float2half_rn(0.f));
-        for (int split = 0; split < 2; ++split)
-            for (int jx = 0; jx < p.Px; ++jx)
-                for (int x = 0; x < nx; ++x) {
-                    const double b = basis_value_d(nx, p.xfreq[jx], x);
-                    const __half hi = __double2half(b);
-                    const __half v = split == 0 ? hi : __double2half(b - (double)__half2float(hi));
-                    const size_t off = (size_t)split * nx * 96u + kmajor_offset((uint32_t)jx, (uint32_t)x, 768u, 128u);
-                    img[off / 2] = v;
-                }
+        for (int g = 0; g < nx / GC; ++g)
+            for (int split = 0; split < 2; ++split)
+                for (int h = 0; h < 2; ++h)
+                    for (int jx = 0; jx < p.Px; ++jx)
+                        for (int m = 0; m < GC; ++m) {
+                            const double b = basis_value_d(nx, p.xfreq[jx], g * GC + m);
+                            const __half hi = __double2half(b);
+                            const __half v = split == 0 ? hi : __double2half(b - (double)__half2float(hi));
+                            const size_t off = (size_t)g * kBxStage + (size_t)split * (kBxStage / 2) +
+                                               kmajor_offset((uint32_t)jx, (uint32_t)(h * GC + m), 768u, 128u);
+                            img[off / 2] = v;
+                        }
         e = cudaMemcpyAsync(t->bximg, img.data(), bx_bytes, cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     }
@@ -603,7 +583,7 @@ cudaError_t forward_tc(const zl_plan_s& p, const float* x, float* out, int R, cu
     const int grid = units < t.num_sms ? units : t.num_sms;
     p.timer.begin(ZL_STAGE_FWD_COLUMN, s);
     fwd_column_tc_kernel<<<grid, kThreadsTc, t.smem, s>>>(tmap, t.pimg, t.bximg, reinterpret_cast<float*>(p.t1),
-                                                          t.d_err, R, p.d.K, p.d.nx, p.d.ny, t.nwp, p.Px, t.pxp);
+                                                          t.d_err, R, p.d.K, p.d.nx, p.d.ny, t.nwp, t.pxp);
     p.timer.end(s);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

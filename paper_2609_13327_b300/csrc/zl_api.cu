@@ -83,6 +83,19 @@ cudaError_t build_tables(zl_plan_s& p, zl::Tables<T>& t, const std::vector<doubl
         isl[j] = (T)(1.0 / std::sqrt(lamS[j]));
         sl[j] = (T)std::sqrt(lamS[j]);
     }
+    // kept y-frequencies and the transposed table of their basis vectors
+    std::vector<int> yslot(ny, -1), pylist;
+    for (int j = 0; j < L; ++j) yslot[py[j]] = 1;
+    for (int q = 0; q < ny; ++q)
+        if (yslot[q] == 1) {
+            yslot[q] = (int)pylist.size();
+            pylist.push_back(q);
+        }
+    std::vector<int> ipy(L);
+    for (int j = 0; j < L; ++j) ipy[j] = yslot[py[j]];
+    std::vector<T> byk((size_t)ny * p.pys, (T)0);
+    for (int y = 0; y < ny; ++y)
+        for (size_t i = 0; i < pylist.size(); ++i) byk[(size_t)y * p.pys + i] = (T)basis_value(ny, pylist[i], y);
     std::vector<int> gstart(Px + 1, 0), gmodes(L);
     for (int j = 0; j < L; ++j) gstart[jxv[j] + 1]++;
     for (int q = 0; q < Px; ++q) gstart[q + 1] += gstart[q];
@@ -96,6 +109,8 @@ cudaError_t build_tables(zl_plan_s& p, zl::Tables<T>& t, const std::vector<doubl
     if ((e = upload(&t.m_py, py, s)) != cudaSuccess) return e;
     if ((e = upload(&t.m_jx, jxv, s)) != cudaSuccess) return e;
     if ((e = upload(&t.grp_start, gstart, s)) != cudaSuccess) return e;
+    if ((e = upload(&t.m_ipy, ipy, s)) != cudaSuccess) return e;
+    if ((e = upload(&t.byk, byk, s)) != cudaSuccess) return e;
     return upload(&t.grp_modes, gmodes, s);
 }
 
@@ -109,6 +124,8 @@ void free_tables(zl::Tables<T>& t) {
     cudaFree(t.m_jx);
     cudaFree(t.grp_start);
     cudaFree(t.grp_modes);
+    cudaFree(t.m_ipy);
+    cudaFree(t.byk);
     t = zl::Tables<T>();
 }
 
@@ -309,6 +326,13 @@ zl_status zl_setup(const zl_desc* desc, const void* Z, const double* spectrum, v
         if (used[q]) xfreq.push_back(q);
     p->Px = (int)xfreq.size();
     p->xfreq = xfreq;
+    {
+        std::vector<char> yused(d.ny, 0);
+        for (int s2 : p->modes) yused[s2 / d.nx] = 1;
+        p->Py = 0;
+        for (char c : yused) p->Py += c;
+        p->pys = (p->Py + 15) / 16 * 16;
+    }
     // forward y-pass keeps the L accumulators in shared memory
     if ((size_t)p->L * p->esize + (size_t)p->Px * p->esize > 96 * 1024 ||
         (size_t)d.K * (p->Px + 32) * p->esize > 160 * 1024) {

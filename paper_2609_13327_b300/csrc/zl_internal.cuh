@@ -26,6 +26,8 @@ struct Tables {
     int* m_jx = nullptr;
     int* grp_start = nullptr;
     int* grp_modes = nullptr;
+    int* m_ipy = nullptr;   // [L] index of mode j's p_y in the list of kept y-frequencies
+    T* byk = nullptr;       // [ny][pys] b_{p_y}(y) of the kept y-frequencies, zero-padded to pys
 };
 
 struct TcOperands;   // tensor-core path state (k_tc.cu)
@@ -54,6 +56,8 @@ struct zl_plan_s {
     int g = 0;              // min(nw, K)
     int L = 0;              // kept modes
     int Px = 0;             // kept x-frequencies
+    int Py = 0;             // kept y-frequencies
+    int pys = 0;            // Py rounded up to 16 (row stride of the kept y-basis table)
     int bad_column = -1;
     std::vector<int> modes; // kept packed indices (host copy)
     std::vector<int> xfreq; // kept x-frequencies (packed x-index), in the order of the x-pass
@@ -62,7 +66,7 @@ struct zl_plan_s {
     // member matrices, [K][nw][nh]: the plan's copy of Z and the pseudo-inverse P (P[k][l][m] = (A_m^+)[k][l])
     void* Zc = nullptr;
     void* P = nullptr;
-    // intermediate of the separable transform, [max_rhs][K][ny][Px]
+    // intermediate of the separable transform: forward [ny][max_rhs][K][ldp], inverse [max_rhs][K][ny][Px]
     void* t1 = nullptr;
     zl::Tables<double> td;
     zl::Tables<float> tf;

@@ -79,3 +79,22 @@ def test_unsupported_shape_runs_cuda_cores(zl):
     lam = basis.spectrum_2d(w.Nx, w.Ny, w.ell_loc)
     plan = zl.zl_setup(torch.from_numpy(Z).cuda(), lam, tau=w.tau, prec="mixed", max_rhs=w.R, nx=w.Nx, ny=w.Ny)
     assert not plan.uses_tc()
+
+
+FULL_TC = [("c2_128x128x10", [0, 255]), ("c3_256x256x32", [1, 62]), ("c5_512x512x16", [2])]
+
+
+@pytest.mark.parametrize("name,sample", FULL_TC, ids=[n for n, _ in FULL_TC])
+def test_tensor_core_full_size_sampled(zl, name, sample):
+    """The 1-GPU benchmark shapes in mixed precision, at full size, sampled right-hand sides."""
+    w = synth.WORKLOADS[name]
+    Z = synth.ensemble(w).astype(np.float32)
+    lam = basis.spectrum_2d(w.Nx, w.Ny, w.ell_loc)
+    plan = zl.zl_setup(torch.from_numpy(Z).cuda(), lam, tau=w.tau, prec="mixed", max_rhs=w.R, nx=w.Nx, ny=w.Ny)
+    assert plan.uses_tc()
+    x = synth.rhs(w, dtype=np.float32)
+    out = zl.zl_apply_left_inverse(plan, torch.from_numpy(x).cuda()).cpu().numpy()
+    assert plan.device_error() == 0
+    oracle = swift.Plan(Z.astype(np.float64), w.Nx, w.Ny, lam, w.tau)
+    ref = swift.apply_left_inverse(oracle, x[sample].astype(np.float64))
+    assert rel_err(out[sample].astype(np.float64), ref) <= TOL_MIXED
