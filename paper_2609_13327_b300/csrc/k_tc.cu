@@ -72,6 +72,30 @@ constexpr uint32_t kWSplit = 32768;    // hi / lo offset inside W
 constexpr uint32_t kBxStage = 3072;    // x-pass basis per group: 2 splits x 2 chunks x 6 row groups x 128 B
 constexpr unsigned long long kWaitCycles = 4000000000ull;   // ~2 s at 2 GHz
 
+// Barrier slots
+enum {
+    B_PFULL = 0,
+    B_PEMPTY = B_PFULL + SP,
+    B_XFULL = B_PEMPTY + SP,
+    B_XEMPTY = B_XFULL + SX,
+    B_BXFULL = B_XEMPTY + SX,
+    B_BXEMPTY = B_BXFULL + SB,
+    B_B1FULL = B_BXEMPTY + SB,
+    B_B1EMPTY = B_B1FULL + 2,
+    B_D1FULL = B_B1EMPTY + 2,
+    B_D1EMPTY,
+    B_WFULL,
+    B_WEMPTY,
+    B_D2FULL,
+    B_D2EMPTY,
+    B_FIN,
+    B_COUNT
+};
+
+// barriers, then the TMEM base-address slot and the abort flag
+constexpr uint32_t kBarBytes = ((B_COUNT * 8u + 8u) + 127u) & ~127u;
+static_assert(B_COUNT * 8 + 8 <= (int)kBarBytes, "barrier region too small");
+
 struct SmemPlan {
     uint32_t pring, xring, bxring, b1, w, bars, total;
 };
@@ -93,30 +117,11 @@ __host__ __device__ inline SmemPlan smem_plan(int nwp) {
     s.w = o;
     o += 2 * kWSplit;
     s.bars = o;
-    o += 256;
+    o += kBarBytes;
     s.total = o;
     return s;
 }
 
-// Barrier slots
-enum {
-    B_PFULL = 0,
-    B_PEMPTY = B_PFULL + SP,
-    B_XFULL = B_PEMPTY + SP,
-    B_XEMPTY = B_XFULL + SX,
-    B_BXFULL = B_XEMPTY + SX,
-    B_BXEMPTY = B_BXFULL + SB,
-    B_B1FULL = B_BXEMPTY + SB,
-    B_B1EMPTY = B_B1FULL + 2,
-    B_D1FULL = B_B1EMPTY + 2,
-    B_D1EMPTY,
-    B_WFULL,
-    B_WEMPTY,
-    B_D2FULL,
-    B_D2EMPTY,
-    B_FIN,
-    B_COUNT
-};
 
 __device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
     const long long t0 = clock64();
