@@ -198,6 +198,33 @@ typedef enum {
 zl_status zl_set_stage_timing(zl_plan plan, int enable);
 zl_status zl_get_stage_times(zl_plan plan, int stage, int* launches, double* total_ms);
 
+/*
+ * zl_apply_left_inverse_static -- the same operator as zl_apply_left_inverse
+ * (x [R][nw][ny*nx] -> x~ [R][K][L], device buffers, stream-ordered), for
+ * callers that cannot allocate device memory when they apply it: a real-time
+ * loop whose device memory budget is fixed at start-up, code running inside a
+ * host callback where allocation calls are not allowed, or a process whose
+ * device memory is owned by another framework's pool.  This call allocates
+ * nothing.  The paper has no counterpart; it is a property of this library.
+ *
+ * It runs the CUDA-core kernels (for ZL_MIXED plans too) and keeps the
+ * intermediate of the separable transform in a 16 MiB scratch array compiled
+ * into libzl, held by every GPU that loads the library until the process
+ * exits.  Right-hand sides are processed in passes of at most
+ * 16 MiB / (K * ny * Px * element size) of them (and at most max_rhs); a plan
+ * for which even one right-hand side needs more than 16 MiB
+ * (K * ny * Px * element size > 16 MiB, Px = kept x-frequencies) is rejected
+ * with ZL_ERR_SHAPE before any work is queued.
+ *
+ * The first call on a device looks up the scratch array's device address
+ * (with that device current) and caches it; make that first call before any
+ * stream capture.  Every call, on every stream, shares the one array, so calls
+ * that overlap on the GPU race: serialise them (one stream, or events).
+ * Nothing in the array needs clearing between calls: each pass overwrites the
+ * part it reads.
+ */
+zl_status zl_apply_left_inverse_static(zl_plan plan, const void* x, void* xt, int R, void* stream);
+
 /* zl_destroy -- free a plan and everything it owns (NULL is a no-op).  The
  * caller must make sure no queued apply still uses it. */
 zl_status zl_destroy(zl_plan plan);

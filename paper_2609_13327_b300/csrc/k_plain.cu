@@ -385,6 +385,26 @@ cudaError_t inverse_plain(const zl_plan_s& p, const Tables<T>& t, const T* M, co
     return cudaGetLastError();
 }
 
+// The forward pass of forward_plain with a caller-chosen intermediate buffer t1
+// (at least R * K * ny * Px elements).  Used by zl_apply_left_inverse_static.
+template <typename T>
+cudaError_t forward_plain_on(const zl_plan_s& p, const Tables<T>& t, const T* M, const T* scale, const T* x, T* out,
+                             int R, cudaStream_t s, T* t1) {
+    const size_t row = (size_t)KC * (p.d.nx + 1) * sizeof(T);
+    cudaError_t e;
+    if (R >= 8 && 8 * row <= kRowSmemBudget) e = launch_fwd_rc<T, 8>(p, x, M, t.bx, t1, R, s);
+    else if (R >= 4 && 4 * row <= kRowSmemBudget) e = launch_fwd_rc<T, 4>(p, x, M, t.bx, t1, R, s);
+    else if (R >= 2 && 2 * row <= kRowSmemBudget) e = launch_fwd_rc<T, 2>(p, x, M, t.bx, t1, R, s);
+    else e = launch_fwd_rc<T, 1>(p, x, M, t.bx, t1, R, s);
+    if (e != cudaSuccess) return e;
+    return launch_ypass<T>(p, t1, p.Px, t.by, t.m_py, t.m_jx, scale, out, R, s, &t);
+}
+
+template cudaError_t forward_plain_on<double>(const zl_plan_s&, const Tables<double>&, const double*, const double*,
+                                              const double*, double*, int, cudaStream_t, double*);
+template cudaError_t forward_plain_on<float>(const zl_plan_s&, const Tables<float>&, const float*, const float*,
+                                             const float*, float*, int, cudaStream_t, float*);
+
 template cudaError_t forward_plain<double>(const zl_plan_s&, const Tables<double>&, const double*, const double*,
                                            const double*, double*, int, cudaStream_t);
 template cudaError_t forward_plain<float>(const zl_plan_s&, const Tables<float>&, const float*, const float*,

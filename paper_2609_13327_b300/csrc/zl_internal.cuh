@@ -92,6 +92,9 @@ template <typename T>
 cudaError_t forward_plain(const zl_plan_s& p, const Tables<T>& t, const T* M, const T* scale, const T* x, T* out,
                           int R, cudaStream_t s);
 template <typename T>
+cudaError_t forward_plain_on(const zl_plan_s& p, const Tables<T>& t, const T* M, const T* scale, const T* x, T* out,
+                             int R, cudaStream_t s, T* t1);
+template <typename T>
 cudaError_t inverse_plain(const zl_plan_s& p, const Tables<T>& t, const T* M, const T* scale, const T* c, T* out,
                           int R, cudaStream_t s);
 

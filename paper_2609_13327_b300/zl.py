@@ -27,7 +27,8 @@ PRECISIONS = {"fp64": ZL_FP64, "fp32": ZL_FP32, "mixed": ZL_MIXED}
 # every symbol declared in include/zl.h
 EXPORTS = ["zl_setup", "zl_get_info", "zl_get_modes", "zl_apply_left_inverse", "zl_apply_left_inverse_host",
            "zl_apply_sqrt", "zl_apply_adjoint", "zl_apply_sqrt_adjoint", "zl_destroy", "zl_status_string",
-           "zl_gaussian_spectrum", "zl_set_stage_timing", "zl_get_stage_times", "zl_get_runtime_info"]
+           "zl_gaussian_spectrum", "zl_set_stage_timing", "zl_get_stage_times", "zl_get_runtime_info",
+           "zl_apply_left_inverse_static"]
 STAGES = {"fwd_column": 0, "fwd_ypass": 1, "inv_ypass": 2, "inv_column": 3}
 
 
@@ -42,7 +43,7 @@ _lib.zl_setup.argtypes = [ctypes.POINTER(zl_desc), _vp, _dp, _vp, ctypes.POINTER
 _lib.zl_get_info.argtypes = [_vp, _ip, _ip, _ip, _llp, _ip]
 _lib.zl_get_modes.argtypes = [_vp, _ip]
 for _name in ("zl_apply_left_inverse", "zl_apply_left_inverse_host", "zl_apply_sqrt", "zl_apply_adjoint",
-              "zl_apply_sqrt_adjoint"):
+              "zl_apply_sqrt_adjoint", "zl_apply_left_inverse_static"):
     getattr(_lib, _name).argtypes = [_vp, _vp, _vp, _int, _vp]
 _lib.zl_destroy.argtypes = [_vp]
 _lib.zl_status_string.argtypes = [_int]
@@ -199,6 +200,12 @@ def zl_apply_left_inverse(plan, x, out=None, stream=None):
     """x~ = Zh^- x: x [R][n_w][n_h] -> x~ [R][K][L]."""
     return _apply(_lib.zl_apply_left_inverse, plan, x, (plan.nw, plan.nh), (plan.K, plan.L), out, stream,
                   "zl_apply_left_inverse")
+
+
+def zl_apply_left_inverse_static(plan, x, out=None, stream=None):
+    """x~ = Zh^- x without any device allocation (scratch in the library's static array)."""
+    return _apply(_lib.zl_apply_left_inverse_static, plan, x, (plan.nw, plan.nh), (plan.K, plan.L), out, stream,
+                  "zl_apply_left_inverse_static")
 
 
 def zl_apply_sqrt_adjoint(plan, x, out=None, stream=None):
