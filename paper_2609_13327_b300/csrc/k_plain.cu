@@ -277,7 +277,22 @@ fwd_ypass_gemm(const T* __restrict__ t1, const T* __restrict__ byk, const int* _
         }
         __syncthreads();
         if (active) {
-            for (int yy = 0; yy < yn; ++yy) {
+            int yy = 0;
+            for (; yy + 3 < yn; yy += 4) {   // four independent loads in flight per thread
+                const T t0 = src[(long long)(y0 + yy) * ystride];
+                const T t1v = src[(long long)(y0 + yy + 1) * ystride];
+                const T t2 = src[(long long)(y0 + yy + 2) * ystride];
+                const T t3 = src[(long long)(y0 + yy + 3) * ystride];
+                const T* b = sby + yy * PYT;
+#pragma unroll
+                for (int i = 0; i < PYT; ++i) {
+                    acc[i] = fma(b[i], t0, acc[i]);
+                    acc[i] = fma(b[PYT + i], t1v, acc[i]);
+                    acc[i] = fma(b[2 * PYT + i], t2, acc[i]);
+                    acc[i] = fma(b[3 * PYT + i], t3, acc[i]);
+                }
+            }
+            for (; yy < yn; ++yy) {
                 const T tv = src[(long long)(y0 + yy) * ystride];
                 const T* b = sby + yy * PYT;
 #pragma unroll
@@ -320,8 +335,11 @@ cudaError_t launch_ypass(const zl_plan_s& p, const T* t1, int ldp, const T* by, 
                          const T* scale, T* out, int R, cudaStream_t s, const Tables<T>* tb = nullptr) {
     const int ny = p.d.ny, K = p.d.K;
     if (tb != nullptr && p.Px <= kThreads) {
+        if (p.Py <= 8) return launch_ypass_gemm<T, 8>(p, t1, ldp, tb->byk, tb->m_ipy, m_jx, scale, out, R, s);
         if (p.Py <= 16) return launch_ypass_gemm<T, 16>(p, t1, ldp, tb->byk, tb->m_ipy, m_jx, scale, out, R, s);
+        if (p.Py <= 24) return launch_ypass_gemm<T, 24>(p, t1, ldp, tb->byk, tb->m_ipy, m_jx, scale, out, R, s);
         if (p.Py <= 32) return launch_ypass_gemm<T, 32>(p, t1, ldp, tb->byk, tb->m_ipy, m_jx, scale, out, R, s);
+        if (p.Py <= 40) return launch_ypass_gemm<T, 40>(p, t1, ldp, tb->byk, tb->m_ipy, m_jx, scale, out, R, s);
         if (p.Py <= 48) return launch_ypass_gemm<T, 48>(p, t1, ldp, tb->byk, tb->m_ipy, m_jx, scale, out, R, s);
         if (p.Py <= 64) return launch_ypass_gemm<T, 64>(p, t1, ldp, tb->byk, tb->m_ipy, m_jx, scale, out, R, s);
     }

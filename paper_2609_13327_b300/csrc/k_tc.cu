@@ -20,11 +20,13 @@
 // Delta^{-1/2} scaling and compaction (the rest of V4, and V5) follow in the
 // CUDA-core kernel fwd_ypass.
 //
-// Warp roles (320 threads): warp 0 lane 0 = TMA producer (x tiles through a
-// 3-D tensor map; the per-column [P_hi; P_lo] images and the per-group x-pass
-// basis by 1-D bulk copies), warp 1 = TMEM allocator + single-thread MMA
-// issuer, warps 2-9 = converters (x tile -> FP16 hi/lo B operand, two groups
-// ahead) and epilogue (TMEM -> W operand; TMEM -> intermediate t1
+// Warp roles (352 threads): warp 0 lane 0 = producer of the per-column
+// [P_hi; P_lo] images and the per-group x-pass basis (1-D bulk copies, a
+// 13-deep ring so each image is requested about one group period before use),
+// warp 1 = TMEM allocator + single-thread MMA issuer, warp 2 lane 0 = producer
+// of the x tiles (3-D tensor map), warps 3-10 = converters (x tile -> FP16
+// hi/lo B operand of the next group, right after the TMEM loads of the
+// current one) and epilogue (TMEM -> W operand; TMEM -> intermediate t1
 // [ny][R][K][pxp]); two epilogue warps share each TMEM lane quarter and split
 // the unit's right-hand sides.  The MMA issue order V1(g), x-pass(g-1) keeps the
 // tensor pipe busy while the epilogue turns D1(g) into W(g).  All waits are bounded; on timeout the kernel records an
@@ -59,11 +61,13 @@ constexpr int RC = 16;                 // right-hand sides per unit (V1 N)
 constexpr int GC = 8;                  // columns per group (one x-pass K-step: 8 columns x 2 halves)
 constexpr int N2 = 48;                 // x-pass N: kept x-frequencies padded
 constexpr int MT = 8;                  // x-pass M tiles: 64 members x 16 rhs / 128
-constexpr int SP = 8;                  // P image ring depth (one group)
+constexpr int SP = 13;                 // P image ring depth: more than a group, so a slot is
+                                       // requested about one group period before its use
 constexpr int SX = 2;                  // x tile ring depth
-constexpr int SB = 2;                  // x-pass basis ring depth
+constexpr int SB = 3;                  // x-pass basis ring depth
 constexpr int NEPI = 8;                // epilogue / converter warps
-constexpr int kThreadsTc = 64 + 32 * NEPI;
+constexpr int kEpiWarp0 = 3;           // warps 0: P/basis producer, 1: MMA, 2: x producer
+constexpr int kThreadsTc = 32 * kEpiWarp0 + 32 * NEPI;
 constexpr int kEpiThreads = 32 * NEPI;
 constexpr uint32_t kD1Col = MT * N2;   // 384: D1 (V1 accumulators) after the x-pass accumulators
 constexpr uint32_t kTmemCols = 512;
@@ -81,8 +85,8 @@ enum {
     B_BXFULL = B_XEMPTY + SX,
     B_BXEMPTY = B_BXFULL + SB,
     B_B1FULL = B_BXEMPTY + SB,
-    B_B1EMPTY = B_B1FULL + 2,
-    B_D1FULL = B_B1EMPTY + 2,
+    B_B1EMPTY,
+    B_D1FULL,
     B_D1EMPTY,
     B_WFULL,
     B_WEMPTY,
@@ -112,7 +116,7 @@ __host__ __device__ inline SmemPlan smem_plan(int nwp) {
     s.bxring = o;
     o += SB * kBxStage;
     s.b1 = o;
-    o += 2 * GC * b1_stride(nwp);
+    o += GC * b1_stride(nwp);
     o = (o + 127u) & ~127u;
     s.w = o;
     o += 2 * kWSplit;
@@ -186,7 +190,6 @@ fwd_column_tc_kernel(const __grid_constant__ CUtensorMap tmap_x, const __half* _
     const uint32_t PBYTES = 256u * nwp;
     const uint32_t XBYTES = 512u * nwp;
     const uint32_t B1S = b1_stride(nwp);
-    const uint32_t B1BUF = GC * B1S;
     const uint32_t b1_sbo = (uint32_t)(nwp / 8) * 128u;
 
     if (tid == 0) {
@@ -202,10 +205,8 @@ fwd_column_tc_kernel(const __grid_constant__ CUtensorMap tmap_x, const __half* _
             mbar_init(&bars[B_BXFULL + i], 1);
             mbar_init(&bars[B_BXEMPTY + i], 1);
         }
-        for (int i = 0; i < 2; ++i) {
-            mbar_init(&bars[B_B1FULL + i], kEpiThreads);
-            mbar_init(&bars[B_B1EMPTY + i], 1);
-        }
+        mbar_init(&bars[B_B1FULL], kEpiThreads);
+        mbar_init(&bars[B_B1EMPTY], 1);
         mbar_init(&bars[B_D1FULL], 1);
         mbar_init(&bars[B_D1EMPTY], kEpiThreads);
         mbar_init(&bars[B_WFULL], kEpiThreads);
@@ -224,19 +225,14 @@ fwd_column_tc_kernel(const __grid_constant__ CUtensorMap tmap_x, const __half* _
     const uint32_t tbase = *tslot;
 
     if (warp == 0) {
-        // ------------------------------------------------------------ producer
+        // ------------------------------------------------------------ producer: basis + P images
         if (lane == 0) {
-            uint32_t pc = 0, xc = 0, bc = 0;
+            uint32_t pc = 0, bc = 0;
             bool ok = true;
             for (uint32_t gi = 0; gi < total_groups && ok; ++gi) {
                 const int u = (int)blockIdx.x + (int)(gi / G) * (int)gridDim.x;
                 const int g = (int)(gi % G);
-                const int y = u / n_rc, r0 = (u % n_rc) * RC;
-                const uint32_t xs = xc % SX, xph = (xc / SX) & 1u;
-                if (!wait_bar(&bars[B_XEMPTY + xs], xph ^ 1u, abort_flag)) { fail(abort_flag, err, 1); ok = false; break; }
-                mbar_arrive_expect_tx(&bars[B_XFULL + xs], XBYTES);
-                tma_load_3d(sxring + xs * XBYTES, &tmap_x, y * nx + g * GC, 0, r0, &bars[B_XFULL + xs]);
-                ++xc;
+                const int y = u / n_rc;
                 const uint32_t bs = bc % SB, bph = (bc / SB) & 1u;
                 if (!wait_bar(&bars[B_BXEMPTY + bs], bph ^ 1u, abort_flag)) { fail(abort_flag, err, 1); ok = false; break; }
                 mbar_arrive_expect_tx(&bars[B_BXFULL + bs], kBxStage);
@@ -253,8 +249,23 @@ fwd_column_tc_kernel(const __grid_constant__ CUtensorMap tmap_x, const __half* _
             }
             // every issued copy must land before the CTA exits
             for (uint32_t s = 0; s < SP; ++s) drain_slot(&bars[B_PFULL + s], pc, s, SP);
-            for (uint32_t s = 0; s < SX; ++s) drain_slot(&bars[B_XFULL + s], xc, s, SX);
             for (uint32_t s = 0; s < SB; ++s) drain_slot(&bars[B_BXFULL + s], bc, s, SB);
+        }
+    } else if (warp == 2) {
+        // ------------------------------------------------------------ producer: x tiles
+        if (lane == 0) {
+            uint32_t xc = 0;
+            for (uint32_t gi = 0; gi < total_groups; ++gi) {
+                const int u = (int)blockIdx.x + (int)(gi / G) * (int)gridDim.x;
+                const int g = (int)(gi % G);
+                const int y = u / n_rc, r0 = (u % n_rc) * RC;
+                const uint32_t xs = xc % SX, xph = (xc / SX) & 1u;
+                if (!wait_bar(&bars[B_XEMPTY + xs], xph ^ 1u, abort_flag)) { fail(abort_flag, err, 1); break; }
+                mbar_arrive_expect_tx(&bars[B_XFULL + xs], XBYTES);
+                tma_load_3d(sxring + xs * XBYTES, &tmap_x, y * nx + g * GC, 0, r0, &bars[B_XFULL + xs]);
+                ++xc;
+            }
+            for (uint32_t s = 0; s < SX; ++s) drain_slot(&bars[B_XFULL + s], xc, s, SX);
         }
     } else if (warp == 1) {
         // ------------------------------------------------------------ MMA issuer
@@ -288,8 +299,7 @@ fwd_column_tc_kernel(const __grid_constant__ CUtensorMap tmap_x, const __half* _
                 return true;
             };
             for (uint32_t gi = 0; gi < total_groups && ok; ++gi) {
-                const uint32_t b = gi & 1u, n = gi >> 1;
-                if (!wait_bar(&bars[B_B1FULL + b], n & 1u, abort_flag) ||
+                if (!wait_bar(&bars[B_B1FULL], gi & 1u, abort_flag) ||
                     !wait_bar(&bars[B_D1EMPTY], (gi & 1u) ^ 1u, abort_flag)) { fail(abort_flag, err, 2); ok = false; break; }
                 tc_fence_after();
                 for (int j = 0; j < GC; ++j) {
@@ -297,7 +307,7 @@ fwd_column_tc_kernel(const __grid_constant__ CUtensorMap tmap_x, const __half* _
                     if (!wait_bar(&bars[B_PFULL + ps], pph, abort_flag)) { fail(abort_flag, err, 2); ok = false; break; }
                     tc_fence_after();
                     const uint32_t a0 = smem_u32(spring + ps * PBYTES);
-                    const uint32_t bhi = smem_u32(sb1 + b * B1BUF + j * B1S);
+                    const uint32_t bhi = smem_u32(sb1 + j * B1S);
                     const uint32_t blo = bhi + 32u * nwp;
                     const uint32_t d = tbase + kD1Col + (uint32_t)j * RC;
                     for (int ks = 0; ks < nwp / 16; ++ks)
@@ -311,7 +321,7 @@ fwd_column_tc_kernel(const __grid_constant__ CUtensorMap tmap_x, const __half* _
                 }
                 if (!ok) break;
                 mma_commit(&bars[B_D1FULL]);
-                mma_commit(&bars[B_B1EMPTY + b]);
+                mma_commit(&bars[B_B1EMPTY]);
                 if (gi > 0 && !xpass(gi - 1)) { fail(abort_flag, err, 2); ok = false; break; }
             }
             if (ok && total_groups > 0 && !xpass(total_groups - 1)) fail(abort_flag, err, 2);
@@ -321,9 +331,9 @@ fwd_column_tc_kernel(const __grid_constant__ CUtensorMap tmap_x, const __half* _
         }
     } else {
         // ------------------------------------------------------------ converters + epilogue
-        const int et = tid - 64;                       // 0 .. kEpiThreads-1
+        const int et = tid - 32 * kEpiWarp0;           // 0 .. kEpiThreads-1
         const int q = warp & 3;                        // TMEM lane quarter this warp may access
-        const int rset = (warp - 2) >> 2;              // rhs half of the unit this warp finalises
+        const int rset = (warp - kEpiWarp0) >> 2;      // rhs half of the unit this warp finalises
         const uint32_t lane_off = (uint32_t)(32 * q) << 16;
         const int kk = (q & 1) * 32 + lane;            // member of this thread's TMEM lane
         const uint32_t half_chunk = q < 2 ? 0u : kWChunk;   // P_hi x -> K-chunk 0, P_lo x -> K-chunk 1
@@ -332,11 +342,10 @@ fwd_column_tc_kernel(const __grid_constant__ CUtensorMap tmap_x, const __half* _
 
         auto convert = [&](uint32_t c) -> bool {
             const uint32_t xs = c % SX, xph = (c / SX) & 1u;
-            const uint32_t b = c & 1u, n = c >> 1;
             if (!warp_wait_bar(&bars[B_XFULL + xs], xph, abort_flag)) return false;
-            if (!warp_wait_bar(&bars[B_B1EMPTY + b], (n & 1u) ^ 1u, abort_flag)) return false;
+            if (!warp_wait_bar(&bars[B_B1EMPTY], (c & 1u) ^ 1u, abort_flag)) return false;
             const float* xt = reinterpret_cast<const float*>(sxring + xs * XBYTES);   // [RC][nwp][GC]
-            uint8_t* b1 = sb1 + b * B1BUF;
+            uint8_t* b1 = sb1;
             const int noct = nwp / 8;
             for (int item = et; item < GC * RC * noct; item += kEpiThreads) {
                 const int j = item % GC, rest = item / GC;
@@ -354,14 +363,14 @@ fwd_column_tc_kernel(const __grid_constant__ CUtensorMap tmap_x, const __half* _
                 *reinterpret_cast<uint4*>(dst + 32u * nwp) = lo;
             }
             fence_proxy_async_smem();
-            mbar_arrive(&bars[B_B1FULL + b]);
+            mbar_arrive(&bars[B_B1FULL]);
             mbar_arrive(&bars[B_XEMPTY + xs]);
             return true;
         };
 
-        while (conv < total_groups && conv < 2) {
-            if (!convert(conv)) { fail(abort_flag, err, 3); ok = false; break; }
-            ++conv;
+        if (total_groups > 0) {
+            if (!convert(0)) { fail(abort_flag, err, 3); ok = false; }
+            conv = 1;
         }
         for (uint32_t gi = 0; gi < total_groups && ok; ++gi) {
             const int u = (int)blockIdx.x + (int)(gi / G) * (int)gridDim.x;
@@ -375,6 +384,11 @@ fwd_column_tc_kernel(const __grid_constant__ CUtensorMap tmap_x, const __half* _
             tmem_ld_wait();
             tc_fence_before();
             mbar_arrive(&bars[B_D1EMPTY]);
+            // ---- the MMA needs group gi+1's x operand next: convert it before the W write
+            if (conv < total_groups) {
+                if (!convert(conv)) { fail(abort_flag, err, 3); ok = false; break; }
+                ++conv;
+            }
             uint4 hi[8], lo[8];
 #pragma unroll
             for (int rl = 0; rl < 8; ++rl) {
@@ -394,11 +408,6 @@ fwd_column_tc_kernel(const __grid_constant__ CUtensorMap tmap_x, const __half* _
             }
             fence_proxy_async_smem();
             mbar_arrive(&bars[B_WFULL]);
-            // ---- keep the converters two groups ahead
-            if (conv < total_groups) {
-                if (!convert(conv)) { fail(abort_flag, err, 3); ok = false; break; }
-                ++conv;
-            }
             // ---- end of a unit: D2 holds the row's x-pass, rows (r, k) -> t1[y][r0 + r][k][0..pxp)
             if ((gi % G) == (uint32_t)G - 1) {
                 const uint32_t ui = gi / G;
