@@ -314,6 +314,106 @@ fwd_ypass_gemm(const T* __restrict__ t1, const T* __restrict__ byk, const int* _
     }
 }
 
+// FP32 y-pass with the t1 rows of the CTA's pairs and the kept y-basis rows streamed
+// through double-buffered shared memory by cp.async (16-byte copies), so that enough
+// bytes are in flight to run at memory speed.  Needs ldp % 4 == 0 (16-byte rows).
+constexpr int kYAsync = 32;
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+template <int PYT>
+__global__ void __launch_bounds__(kThreads)
+fwd_ypass_async(const float* __restrict__ t1, const float* __restrict__ byk, const int* __restrict__ m_ipy,
+                const int* __restrict__ m_jx, const float* __restrict__ scale, float* __restrict__ out,
+                int npairs, int ppc, int ny, int Px, int ldp, int L, int pys) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int pw = ppc * ldp;                                   // floats of one y-row of this CTA
+    float* st = reinterpret_cast<float*>(smem_raw);             // [2][kYAsync][pw]
+    float* sb = st + 2 * kYAsync * pw;                          // [2][kYAsync][PYT]
+    float* sout = sb + 2 * kYAsync * PYT;                       // [ppc][PYT][Px]
+    const int tid = threadIdx.x;
+    const int pl = tid / Px, jx = tid - pl * Px;
+    const long long pair0 = (long long)blockIdx.x * ppc;
+    const int npl = (int)min((long long)ppc, npairs - pair0);  // pairs this CTA really has
+    const bool active = pl < npl;
+    const long long ystride = (long long)npairs * ldp;
+    const int nchunk = (ny + kYAsync - 1) / kYAsync;
+    auto issue = [&](int c) {
+        const int y0 = c * kYAsync, yn = min(kYAsync, ny - y0);
+        float* dt = st + (c & 1) * kYAsync * pw;
+        float* dbk = sb + (c & 1) * kYAsync * PYT;
+        const int q = npl * ldp / 4;                            // 16-byte pieces per y-row
+        for (int e = tid; e < yn * q; e += blockDim.x) {
+            const int yy = e / q, i = e - yy * q;
+            cp_async16(dt + yy * pw + 4 * i, t1 + (y0 + yy) * ystride + pair0 * ldp + 4 * i);
+        }
+        const int qb = PYT / 4;
+        for (int e = tid; e < yn * qb; e += blockDim.x) {
+            const int yy = e / qb, i = e - yy * qb;
+            cp_async16(dbk + yy * PYT + 4 * i, byk + (long long)(y0 + yy) * pys + 4 * i);
+        }
+        cp_async_commit();
+    };
+    float acc[PYT];
+#pragma unroll
+    for (int i = 0; i < PYT; ++i) acc[i] = 0.f;
+    issue(0);
+    for (int c = 0; c < nchunk; ++c) {
+        if (c + 1 < nchunk) {
+            issue(c + 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+        const int yn = min(kYAsync, ny - c * kYAsync);
+        const float* tt = st + (c & 1) * kYAsync * pw + pl * ldp + jx;
+        const float* bb = sb + (c & 1) * kYAsync * PYT;
+        if (active) {
+            for (int yy = 0; yy < yn; ++yy) {
+                const float tv = tt[yy * pw];
+                const float* b = bb + yy * PYT;
+#pragma unroll
+                for (int i = 0; i < PYT; ++i) acc[i] = fmaf(b[i], tv, acc[i]);
+            }
+        }
+        __syncthreads();   // the buffer of chunk c is refilled by issue(c + 2)
+    }
+    if (active) {
+        float* so = sout + (size_t)pl * PYT * Px;
+#pragma unroll
+        for (int i = 0; i < PYT; ++i) so[i * Px + jx] = acc[i];
+    }
+    __syncthreads();
+    for (int pp = 0; pp < npl; ++pp) {
+        const float* so = sout + (size_t)pp * PYT * Px;
+        float* o = out + (pair0 + pp) * L;
+        for (int j = tid; j < L; j += blockDim.x) o[j] = so[m_ipy[j] * Px + m_jx[j]] * scale[j];
+    }
+}
+
+template <int PYT>
+cudaError_t launch_ypass_async(const zl_plan_s& p, const float* t1, int ldp, const float* byk, const int* m_ipy,
+                               const int* m_jx, const float* scale, float* out, int R, cudaStream_t s) {
+    const int npairs = R * p.d.K;
+    const int ppc = kThreads / p.Px;
+    const size_t smem = ((size_t)2 * kYAsync * ppc * ldp + 2 * kYAsync * PYT + (size_t)ppc * PYT * p.Px) * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(fwd_ypass_async<PYT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int grid = (npairs + ppc - 1) / ppc;
+    p.timer.begin(ZL_STAGE_FWD_YPASS, s);
+    fwd_ypass_async<PYT><<<grid, kThreads, smem, s>>>(t1, byk, m_ipy, m_jx, scale, out, npairs, ppc, p.d.ny, p.Px, ldp,
+                                                      p.L, p.pys);
+    p.timer.end(s);
+    return cudaGetLastError();
+}
+
 template <typename T, int PYT>
 cudaError_t launch_ypass_gemm(const zl_plan_s& p, const T* t1, int ldp, const T* byk, const int* m_ipy,
                               const int* m_jx, const T* scale, T* out, int R, cudaStream_t s) {
@@ -358,6 +458,15 @@ cudaError_t launch_ypass(const zl_plan_s& p, const T* t1, int ldp, const T* by, 
 
 cudaError_t forward_ypass_f32(const zl_plan_s& p, const float* t1, int ldp, const float* scale, float* out, int R,
                               cudaStream_t s) {
+    // 16-byte rows and a kept y-basis that fits the register tile: the streaming form
+    if (ldp % 4 == 0 && p.Px <= kThreads && p.pys % 4 == 0 && (size_t)(kThreads / p.Px) * ldp * 2 * kYAsync * 4 <= 160 * 1024) {
+        const Tables<float>& t = p.tf;
+        if (p.Py <= 16) return launch_ypass_async<16>(p, t1, ldp, t.byk, t.m_ipy, t.m_jx, scale, out, R, s);
+        if (p.Py <= 24) return launch_ypass_async<24>(p, t1, ldp, t.byk, t.m_ipy, t.m_jx, scale, out, R, s);
+        if (p.Py <= 32) return launch_ypass_async<32>(p, t1, ldp, t.byk, t.m_ipy, t.m_jx, scale, out, R, s);
+        if (p.Py <= 40) return launch_ypass_async<40>(p, t1, ldp, t.byk, t.m_ipy, t.m_jx, scale, out, R, s);
+        if (p.Py <= 48) return launch_ypass_async<48>(p, t1, ldp, t.byk, t.m_ipy, t.m_jx, scale, out, R, s);
+    }
     return launch_ypass<float>(p, t1, ldp, p.tf.by, p.tf.m_py, p.tf.m_jx, scale, out, R, s, &p.tf);
 }
 

@@ -23,6 +23,8 @@
 // Warp roles (352 threads): warp 0 lane 0 = producer of the per-column
 // [P_hi; P_lo] images and the per-group x-pass basis (1-D bulk copies, a
 // 13-deep ring so each image is requested about one group period before use),
+// and the MMA thread commits only twice per group (one tcgen05.commit per
+// barrier costs the single issuing thread far more than an MMA does),
 // warp 1 = TMEM allocator + single-thread MMA issuer, warp 2 lane 0 = producer
 // of the x tiles (3-D tensor map), warps 3-10 = converters (x tile -> FP16
 // hi/lo B operand of the next group, right after the TMEM loads of the
@@ -76,21 +78,22 @@ constexpr uint32_t kWSplit = 32768;    // hi / lo offset inside W
 constexpr uint32_t kBxStage = 3072;    // x-pass basis per group: 2 splits x 2 chunks x 6 row groups x 128 B
 constexpr unsigned long long kWaitCycles = 4000000000ull;   // ~2 s at 2 GHz
 
-// Barrier slots
+// Barrier slots.  The MMA thread commits once per group for V1 and once for the x-pass,
+// each into a ring of kDone barriers (group gi -> slot gi % kDone): every consumer that must
+// know "V1 / x-pass of group g has completed" waits there, and kDone > the largest lag of
+// any waiter keeps the phase parity unambiguous.
+constexpr int kDone = 4;
+constexpr uint32_t kL2Ahead = 2;       // groups between an L2 prefetch and the shared-memory load
 enum {
     B_PFULL = 0,
-    B_PEMPTY = B_PFULL + SP,
-    B_XFULL = B_PEMPTY + SP,
+    B_XFULL = B_PFULL + SP,
     B_XEMPTY = B_XFULL + SX,
     B_BXFULL = B_XEMPTY + SX,
-    B_BXEMPTY = B_BXFULL + SB,
-    B_B1FULL = B_BXEMPTY + SB,
-    B_B1EMPTY,
-    B_D1FULL,
+    B_V1DONE = B_BXFULL + SB,
+    B_XDONE = B_V1DONE + kDone,
+    B_B1FULL = B_XDONE + kDone,
     B_D1EMPTY,
     B_WFULL,
-    B_WEMPTY,
-    B_D2FULL,
     B_D2EMPTY,
     B_FIN,
     B_COUNT
@@ -127,11 +130,14 @@ __host__ __device__ inline SmemPlan smem_plan(int nwp) {
 }
 
 
+// Bounded wait.  The fast path (phase already complete) is one try_wait; the clock and the
+// abort flag are looked at only every 1024 polls, so waits cost the single-thread roles little.
 __device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+    if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
-    for (uint32_t i = 0;; ++i) {
+    for (uint32_t i = 1;; ++i) {
         if (mbar_try_wait(bar, parity)) return true;
-        if ((i & 255u) == 255u) {
+        if ((i & 1023u) == 0u) {
             if (*abort_flag) return false;
             if ((unsigned long long)(clock64() - t0) > kWaitCycles) return false;
         }
@@ -165,10 +171,12 @@ __device__ __forceinline__ void drain_slot(uint64_t* bar, uint32_t issued, uint3
     while (!mbar_try_wait(bar, (n - 1) & 1u) && (unsigned long long)(clock64() - t0) < kWaitCycles) {}
 }
 
+template <int NWP>
 __global__ void __launch_bounds__(kThreadsTc, 1)
 fwd_column_tc_kernel(const __grid_constant__ CUtensorMap tmap_x, const __half* __restrict__ pimg,
                      const uint8_t* __restrict__ bximg, float* __restrict__ t1, int* __restrict__ err,
-                     int R, int K, int nx, int ny, int nwp, int pxp) {
+                     int R, int K, int nx, int ny, int pxp) {
+    constexpr int nwp = NWP;
     extern __shared__ __align__(1024) uint8_t smem[];
     const SmemPlan sp = smem_plan(nwp);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + sp.bars);
@@ -187,31 +195,25 @@ fwd_column_tc_kernel(const __grid_constant__ CUtensorMap tmap_x, const __half* _
     // units of this CTA: blockIdx.x + i * gridDim.x; groups are numbered across them
     const int my_units = blockIdx.x < units ? (units - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     const uint32_t total_groups = (uint32_t)my_units * (uint32_t)G;
-    const uint32_t PBYTES = 256u * nwp;
-    const uint32_t XBYTES = 512u * nwp;
-    const uint32_t B1S = b1_stride(nwp);
-    const uint32_t b1_sbo = (uint32_t)(nwp / 8) * 128u;
+    constexpr uint32_t PBYTES = 256u * NWP;
+    constexpr uint32_t XBYTES = 512u * NWP;
+    constexpr uint32_t B1S = 64u * NWP + 16u;
+    constexpr uint32_t b1_sbo = (uint32_t)(NWP / 8) * 128u;
 
     if (tid == 0) {
-        for (int i = 0; i < SP; ++i) {
-            mbar_init(&bars[B_PFULL + i], 1);
-            mbar_init(&bars[B_PEMPTY + i], 1);
-        }
+        for (int i = 0; i < SP; ++i) mbar_init(&bars[B_PFULL + i], 1);
         for (int i = 0; i < SX; ++i) {
             mbar_init(&bars[B_XFULL + i], 1);
             mbar_init(&bars[B_XEMPTY + i], kEpiThreads);
         }
-        for (int i = 0; i < SB; ++i) {
-            mbar_init(&bars[B_BXFULL + i], 1);
-            mbar_init(&bars[B_BXEMPTY + i], 1);
+        for (int i = 0; i < SB; ++i) mbar_init(&bars[B_BXFULL + i], 1);
+        for (int i = 0; i < kDone; ++i) {
+            mbar_init(&bars[B_V1DONE + i], 1);
+            mbar_init(&bars[B_XDONE + i], 1);
         }
         mbar_init(&bars[B_B1FULL], kEpiThreads);
-        mbar_init(&bars[B_B1EMPTY], 1);
-        mbar_init(&bars[B_D1FULL], 1);
         mbar_init(&bars[B_D1EMPTY], kEpiThreads);
         mbar_init(&bars[B_WFULL], kEpiThreads);
-        mbar_init(&bars[B_WEMPTY], 1);
-        mbar_init(&bars[B_D2FULL], 1);
         mbar_init(&bars[B_D2EMPTY], kEpiThreads);
         mbar_init(&bars[B_FIN], 1);
         *abort_flag = 0;
@@ -233,18 +235,33 @@ fwd_column_tc_kernel(const __grid_constant__ CUtensorMap tmap_x, const __half* _
                 const int u = (int)blockIdx.x + (int)(gi / G) * (int)gridDim.x;
                 const int g = (int)(gi % G);
                 const int y = u / n_rc;
-                const uint32_t bs = bc % SB, bph = (bc / SB) & 1u;
-                if (!wait_bar(&bars[B_BXEMPTY + bs], bph ^ 1u, abort_flag)) { fail(abort_flag, err, 1); ok = false; break; }
+                // basis stage gi % SB was last used by the x-pass of group gi - SB
+                const uint32_t bs = bc % SB;
+                if (bc >= SB) {
+                    const uint32_t gp = bc - SB;
+                    if (!wait_bar(&bars[B_XDONE + gp % kDone], (gp / kDone) & 1u, abort_flag)) { fail(abort_flag, err, 1); ok = false; break; }
+                }
                 mbar_arrive_expect_tx(&bars[B_BXFULL + bs], kBxStage);
                 bulk_g2s(sbxring + bs * kBxStage, bximg + (size_t)g * kBxStage, kBxStage, &bars[B_BXFULL + bs]);
                 ++bc;
                 for (int j = 0; j < GC; ++j) {
-                    const uint32_t ps = pc % SP, pph = (pc / SP) & 1u;
-                    if (!wait_bar(&bars[B_PEMPTY + ps], pph ^ 1u, abort_flag)) { fail(abort_flag, err, 1); ok = false; break; }
+                    // image slot pc % SP was last used by load pc - SP, i.e. by V1 of group (pc - SP) / GC
+                    const uint32_t ps = pc % SP;
+                    if (pc >= SP) {
+                        const uint32_t gp = (pc - SP) / GC;
+                        if (!wait_bar(&bars[B_V1DONE + gp % kDone], (gp / kDone) & 1u, abort_flag)) { fail(abort_flag, err, 1); ok = false; break; }
+                    }
                     mbar_arrive_expect_tx(&bars[B_PFULL + ps], PBYTES);
                     const size_t col = (size_t)y * nx + (size_t)g * GC + j;
                     bulk_g2s(spring + ps * PBYTES, pimg + col * 128u * nwp, PBYTES, &bars[B_PFULL + ps]);
                     ++pc;
+                    // warm L2 with the image this CTA loads two groups later
+                    const uint32_t ga = gi + kL2Ahead;
+                    if (ga < total_groups) {
+                        const int ua = (int)blockIdx.x + (int)(ga / G) * (int)gridDim.x;
+                        const size_t cola = (size_t)(ua / n_rc) * nx + (size_t)(ga % G) * GC + j;
+                        prefetch_l2(pimg + cola * 128u * nwp, PBYTES);
+                    }
                 }
             }
             // every issued copy must land before the CTA exits
@@ -264,15 +281,26 @@ fwd_column_tc_kernel(const __grid_constant__ CUtensorMap tmap_x, const __half* _
                 mbar_arrive_expect_tx(&bars[B_XFULL + xs], XBYTES);
                 tma_load_3d(sxring + xs * XBYTES, &tmap_x, y * nx + g * GC, 0, r0, &bars[B_XFULL + xs]);
                 ++xc;
+                const uint32_t ga = gi + kL2Ahead;
+                if (ga < total_groups) {
+                    const int ua = (int)blockIdx.x + (int)(ga / G) * (int)gridDim.x;
+                    prefetch_l2_3d(&tmap_x, (ua / n_rc) * nx + (int)(ga % G) * GC, 0, (ua % n_rc) * RC);
+                }
             }
             for (uint32_t s = 0; s < SX; ++s) drain_slot(&bars[B_XFULL + s], xc, s, SX);
         }
     } else if (warp == 1) {
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
-            const uint32_t idesc_v1 = idesc_f16_f32(128, RC);
-            const uint32_t idesc_x = idesc_f16_f32(128, N2);
-            const uint32_t a_sbo = (uint32_t)(nwp / 8) * 128u;
+            constexpr uint32_t idesc_v1 = idesc_f16_f32(128, RC);
+            constexpr uint32_t idesc_x = idesc_f16_f32(128, N2);
+            constexpr uint32_t a_sbo = (uint32_t)(NWP / 8) * 128u;
+            // Base descriptors: an operand b bytes further on is the base plus (b >> 4) in the
+            // start-address field, so each MMA below costs one 64-bit add per operand.
+            const uint64_t dA0 = smem_desc(smem_u32(spring), 128u, a_sbo);
+            const uint64_t dB0 = smem_desc(smem_u32(sb1), 128u, b1_sbo);
+            const uint64_t dW0 = smem_desc(smem_u32(sw), kWChunk, 128u);
+            const uint64_t dX0 = smem_desc(smem_u32(sbxring), 768u, 128u);
             uint32_t pc = 0;
             bool ok = true;
             // x-pass of group gi (W and basis stage of gi ready); first of a unit overwrites D2
@@ -283,45 +311,42 @@ fwd_column_tc_kernel(const __grid_constant__ CUtensorMap tmap_x, const __half* _
                 const bool first = (gi % G) == 0;
                 if (first && !wait_bar(&bars[B_D2EMPTY], ((gi / G) & 1u) ^ 1u, abort_flag)) return false;
                 tc_fence_after();
-                const uint32_t bhi = smem_u32(sbxring + bs * kBxStage), blo = bhi + kBxStage / 2;
-                const uint64_t dbhi = smem_desc(bhi, 768u, 128u), dblo = smem_desc(blo, 768u, 128u);
-                for (int t = 0; t < MT; ++t) {
-                    const uint32_t ahi = smem_u32(sw) + (uint32_t)t * 2048u;
-                    const uint64_t dahi = smem_desc(ahi, kWChunk, 128u), dalo = smem_desc(ahi + kWSplit, kWChunk, 128u);
-                    const uint32_t d = tbase + (uint32_t)t * N2;
-                    mma_f16(d, dahi, dbhi, idesc_x, first ? 0u : 1u);
-                    mma_f16(d, dalo, dbhi, idesc_x, 1u);
-                    mma_f16(d, dahi, dblo, idesc_x, 1u);
-                }
-                mma_commit(&bars[B_WEMPTY]);
-                mma_commit(&bars[B_BXEMPTY + bs]);
-                if ((gi % G) == (uint32_t)G - 1) mma_commit(&bars[B_D2FULL]);
+                const uint64_t dbhi = dX0 + ((bs * kBxStage) >> 4);
+                const uint64_t dblo = dbhi + ((kBxStage / 2) >> 4);
+                const uint32_t acc0 = first ? 0u : 1u;
+                // product-major across the eight row tiles (independent accumulators back to back)
+#pragma unroll
+                for (int t = 0; t < MT; ++t) mma_f16(tbase + (uint32_t)(t * N2), dW0 + ((t * 2048u) >> 4), dbhi, idesc_x, acc0);
+#pragma unroll
+                for (int t = 0; t < MT; ++t)
+                    mma_f16(tbase + (uint32_t)(t * N2), dW0 + ((kWSplit + t * 2048u) >> 4), dbhi, idesc_x, 1u);
+#pragma unroll
+                for (int t = 0; t < MT; ++t) mma_f16(tbase + (uint32_t)(t * N2), dW0 + ((t * 2048u) >> 4), dblo, idesc_x, 1u);
+                mma_commit(&bars[B_XDONE + gi % kDone]);   // W, the basis stage and (last group) D2
                 return true;
             };
             for (uint32_t gi = 0; gi < total_groups && ok; ++gi) {
                 if (!wait_bar(&bars[B_B1FULL], gi & 1u, abort_flag) ||
                     !wait_bar(&bars[B_D1EMPTY], (gi & 1u) ^ 1u, abort_flag)) { fail(abort_flag, err, 2); ok = false; break; }
+                // column by column: each column's four MMAs start as soon as its image has landed
                 tc_fence_after();
+#pragma unroll
                 for (int j = 0; j < GC; ++j) {
-                    const uint32_t ps = pc % SP, pph = (pc / SP) & 1u;
+                    const uint32_t ps = (pc + j) % SP, pph = ((pc + j) / SP) & 1u;
                     if (!wait_bar(&bars[B_PFULL + ps], pph, abort_flag)) { fail(abort_flag, err, 2); ok = false; break; }
                     tc_fence_after();
-                    const uint32_t a0 = smem_u32(spring + ps * PBYTES);
-                    const uint32_t bhi = smem_u32(sb1 + j * B1S);
-                    const uint32_t blo = bhi + 32u * nwp;
-                    const uint32_t d = tbase + kD1Col + (uint32_t)j * RC;
-                    for (int ks = 0; ks < nwp / 16; ++ks)
-                        mma_f16(d, smem_desc(a0 + ks * 256u, 128u, a_sbo), smem_desc(bhi + ks * 256u, 128u, b1_sbo),
-                                idesc_v1, ks > 0);
-                    for (int ks = 0; ks < nwp / 16; ++ks)
-                        mma_f16(d, smem_desc(a0 + ks * 256u, 128u, a_sbo), smem_desc(blo + ks * 256u, 128u, b1_sbo),
-                                idesc_v1, 1u);
-                    mma_commit(&bars[B_PEMPTY + ps]);
-                    ++pc;
+                    const uint64_t da = dA0 + ((ps * PBYTES) >> 4);
+#pragma unroll
+                    for (int half = 0; half < 2; ++half)             // B = x_hi, then x_lo
+#pragma unroll
+                        for (int ks = 0; ks < NWP / 16; ++ks)
+                            mma_f16(tbase + kD1Col + (uint32_t)(j * RC), da + (uint64_t)(ks * 16),
+                                    dB0 + (uint64_t)((j * B1S + half * 32u * NWP + ks * 256u) >> 4), idesc_v1,
+                                    (half | ks) ? 1u : 0u);
                 }
                 if (!ok) break;
-                mma_commit(&bars[B_D1FULL]);
-                mma_commit(&bars[B_B1EMPTY]);
+                pc += GC;
+                mma_commit(&bars[B_V1DONE + gi % kDone]);   // D1, B1 and the group's eight image slots
                 if (gi > 0 && !xpass(gi - 1)) { fail(abort_flag, err, 2); ok = false; break; }
             }
             if (ok && total_groups > 0 && !xpass(total_groups - 1)) fail(abort_flag, err, 2);
@@ -343,7 +368,7 @@ fwd_column_tc_kernel(const __grid_constant__ CUtensorMap tmap_x, const __half* _
         auto convert = [&](uint32_t c) -> bool {
             const uint32_t xs = c % SX, xph = (c / SX) & 1u;
             if (!warp_wait_bar(&bars[B_XFULL + xs], xph, abort_flag)) return false;
-            if (!warp_wait_bar(&bars[B_B1EMPTY], (c & 1u) ^ 1u, abort_flag)) return false;
+            // B1 is free: the caller has seen V1 of group c - 1 complete
             const float* xt = reinterpret_cast<const float*>(sxring + xs * XBYTES);   // [RC][nwp][GC]
             uint8_t* b1 = sb1;
             const int noct = nwp / 8;
@@ -376,7 +401,7 @@ fwd_column_tc_kernel(const __grid_constant__ CUtensorMap tmap_x, const __half* _
             const int u = (int)blockIdx.x + (int)(gi / G) * (int)gridDim.x;
             const int y = u / n_rc, r0 = (u % n_rc) * RC;
             // ---- D1 of group gi: 8 columns x 8 rhs of this thread's lane
-            if (!warp_wait_bar(&bars[B_D1FULL], gi & 1u, abort_flag)) { fail(abort_flag, err, 3); ok = false; break; }
+            if (!warp_wait_bar(&bars[B_V1DONE + gi % kDone], (gi / kDone) & 1u, abort_flag)) { fail(abort_flag, err, 3); ok = false; break; }
             tc_fence_after();
             uint32_t v[GC][8];
 #pragma unroll
@@ -398,7 +423,8 @@ fwd_column_tc_kernel(const __grid_constant__ CUtensorMap tmap_x, const __half* _
                 split2(__uint_as_float(v[6][rl]), __uint_as_float(v[7][rl]), hi[rl].w, lo[rl].w);
             }
             // ---- W: rows (r, k), K-chunk = half (P_hi x or P_lo x), 8 columns per 16-byte row
-            if (!warp_wait_bar(&bars[B_WEMPTY], (gi & 1u) ^ 1u, abort_flag)) { fail(abort_flag, err, 3); ok = false; break; }
+            // W is free once the x-pass of the previous group has completed
+            if (gi > 0 && !warp_wait_bar(&bars[B_XDONE + (gi - 1) % kDone], ((gi - 1) / kDone) & 1u, abort_flag)) { fail(abort_flag, err, 3); ok = false; break; }
 #pragma unroll
             for (int rl = 0; rl < 8; ++rl) {
                 const uint32_t row = (uint32_t)(rset * 8 + rl) * 64u + (uint32_t)kk;
@@ -410,8 +436,7 @@ fwd_column_tc_kernel(const __grid_constant__ CUtensorMap tmap_x, const __half* _
             mbar_arrive(&bars[B_WFULL]);
             // ---- end of a unit: D2 holds the row's x-pass, rows (r, k) -> t1[y][r0 + r][k][0..pxp)
             if ((gi % G) == (uint32_t)G - 1) {
-                const uint32_t ui = gi / G;
-                if (!warp_wait_bar(&bars[B_D2FULL], ui & 1u, abort_flag)) { fail(abort_flag, err, 3); ok = false; break; }
+                if (!warp_wait_bar(&bars[B_XDONE + gi % kDone], (gi / kDone) & 1u, abort_flag)) { fail(abort_flag, err, 3); ok = false; break; }
                 tc_fence_after();
 #pragma unroll 1
                 for (int t = rset; t < MT; t += 2) {
@@ -553,7 +578,9 @@ zl_status tc_prepare(zl_plan_s& p, cudaStream_t s) {
         }
     }
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(fwd_column_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t->smem);
+        e = t->nwp == 16
+                ? cudaFuncSetAttribute(fwd_column_tc_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t->smem)
+                : cudaFuncSetAttribute(fwd_column_tc_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t->smem);
     if (e != cudaSuccess) {
         cudaFree(t->pimg);
         cudaFree(t->bximg);
@@ -596,8 +623,12 @@ cudaError_t forward_tc(const zl_plan_s& p, const float* x, float* out, int R, cu
     const int units = p.d.ny * ((R + RC - 1) / RC);
     const int grid = units < t.num_sms ? units : t.num_sms;
     p.timer.begin(ZL_STAGE_FWD_COLUMN, s);
-    fwd_column_tc_kernel<<<grid, kThreadsTc, t.smem, s>>>(tmap, t.pimg, t.bximg, reinterpret_cast<float*>(p.t1),
-                                                          t.d_err, R, p.d.K, p.d.nx, p.d.ny, t.nwp, t.pxp);
+    if (t.nwp == 16)
+        fwd_column_tc_kernel<16><<<grid, kThreadsTc, t.smem, s>>>(tmap, t.pimg, t.bximg, reinterpret_cast<float*>(p.t1),
+                                                                  t.d_err, R, p.d.K, p.d.nx, p.d.ny, t.pxp);
+    else
+        fwd_column_tc_kernel<32><<<grid, kThreadsTc, t.smem, s>>>(tmap, t.pimg, t.bximg, reinterpret_cast<float*>(p.t1),
+                                                                  t.d_err, R, p.d.K, p.d.nx, p.d.ny, t.pxp);
     p.timer.end(s);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
