@@ -5,34 +5,53 @@
 // column m of the row the per-column product of step V1 (Sec. 3.9),
 //     w^(m) = A_m^+ x^(m),   a K x n_w by n_w x RC product,
 // runs on the tensor cores with FP16 operand splits P = P_hi + P_lo and
-// x = x_hi + x_lo: the A operand stacks [P_hi; P_lo] (M = 128 rows = 2 x 64
-// members), so two MMAs (B = x_hi, then B = x_lo) leave all four partial
-// products in TMEM (lanes k: P_hi x, lanes 64 + k: P_lo x).  The epilogue warps
-// split each half into FP16 hi/lo again and write it as the A operand W of the
-// x-pass, whose rows are the (rhs, member) pairs of the unit and whose K
-// dimension runs along the grid row: one K-step per 8-column group, K-chunk 0
-// holding the P_hi x half and K-chunk 1 the P_lo x half of the same 8 columns,
-// so the x-pass MMA itself adds the two halves (its basis operand repeats the
-// 8 columns' basis values in both chunks).  The x-pass multiplies by the pruned
-// real-Fourier basis of the row (N = 48 >= Px kept x-frequencies, hi/lo split,
-// three products) and accumulates the whole row in TMEM.  The regrouping of w^(m) into member segments (steps V2-V3, the
-// paper's inter-processor exchange) thus never leaves the SM.  The y-pass,
-// Delta^{-1/2} scaling and compaction (the rest of V4, and V5) follow in the
-// CUDA-core kernel fwd_ypass.
+// x = x_hi + x_lo.  One MMA per K-step yields all four partial products: the A
+// operand stacks [P_hi; P_lo] along M (128 rows = 2 x 64 members) and the B
+// operand stacks [x_hi; x_lo] along N (32 = 2 x RC), so TMEM lane k holds
+// P_hi x_hi | P_hi x_lo and lane 64 + k holds P_lo x_hi | P_lo x_lo.  The
+// epilogue adds the two N halves, giving P_hi x (lanes < 64) and the small
+// correction P_lo x (lanes >= 64), and writes the A operand W of the x-pass:
+// P_hi x split again into FP16 hi/lo (W_hi, W_lo), P_lo x rounded once to FP16
+// (W_c, its own rounding error is 2^-11 of a term that is itself 2^-11 of w).
+// The x-pass multiplies W by the pruned real-Fourier basis of the row (N = 48
+// >= P_x kept x-frequencies, b = b_hi + b_lo) and accumulates the whole row in
+// TMEM; its K dimension runs along the grid row, 8 columns per K-chunk, and two
+// MMAs per 128-row tile and 8-column group give
+//     W_hi b_hi + W_c b_hi   (K-chunks [W_hi | W_c]  x [b_hi | b_hi])
+//     W_lo b_hi + W_hi b_lo  (K-chunks [W_lo | W_hi] x [b_hi | b_lo]),
+// dropping only the 2^-22 terms W_lo b_lo and W_c b_lo.  The regrouping of
+// w^(m) into member segments (steps V2-V3, the paper's inter-processor
+// exchange) thus never leaves the SM.  The y-pass, Delta^{-1/2} scaling and
+// compaction (the rest of V4, and V5) follow in the CUDA-core kernel fwd_ypass.
 //
-// Warp roles (352 threads): warp 0 lane 0 = producer of the per-column
-// [P_hi; P_lo] images and the per-group x-pass basis (1-D bulk copies, a
-// 13-deep ring so each image is requested about one group period before use),
-// and the MMA thread commits only twice per group (one tcgen05.commit per
-// barrier costs the single issuing thread far more than an MMA does),
-// warp 1 = TMEM allocator + single-thread MMA issuer, warp 2 lane 0 = producer
-// of the x tiles (3-D tensor map), warps 3-10 = converters (x tile -> FP16
-// hi/lo B operand of the next group, right after the TMEM loads of the
-// current one) and epilogue (TMEM -> W operand; TMEM -> intermediate t1
-// [ny][R][K][pxp]); two epilogue warps share each TMEM lane quarter and split
-// the unit's right-hand sides.  The MMA issue order V1(g), x-pass(g-1) keeps the
-// tensor pipe busy while the epilogue turns D1(g) into W(g).  All waits are bounded; on timeout the kernel records an
-// error code, drains its own copies, frees TMEM and returns.
+// Shared-memory bandwidth (about 128 B per clock, shared by the tensor pipe's
+// operand reads, the bulk copies and the warps' loads and stores) bounds this
+// kernel, so the operand layout minimises bytes moved per column: one 4 KB A
+// read per V1 K-step, one conversion pass over x, 48 KB of W per 8 columns.
+//
+// TMEM: 384 columns of x-pass accumulators (8 tiles x 48) and 128 columns of
+// V1 accumulators, i.e. 4 grid columns x 32; V1 therefore runs in half-groups
+// of 4 columns.  The MMA order V1(2g), x-pass(g-1), V1(2g+1) keeps the tensor
+// pipe busy while the epilogue drains the first half-group, and because the
+// pipe completes MMAs in issue order, the commit after V1(2g+1) also reports
+// the x-pass of group g-1: the single issuing thread commits only twice per
+// group (a commit holds it for about as long as the MMAs still queued).
+//
+// Operand supply: the engine behind the bulk copies spends a roughly fixed
+// time per copy, so operands arrive in few, large copies: the [P_hi; P_lo]
+// images of a half-group's four columns are contiguous in the plan's image
+// array and land in one 4 x 8 KB copy (a 3-slot ring), the x tile of a group
+// in one 3-D tensor-map load, the basis of a group in one 2.3 KB copy, and one
+// L2 prefetch per group warms the images needed two groups later.
+//
+// Warp roles (352 threads): warp 0 lane 0 = producer of the pseudo-inverse
+// images and of the per-group x-pass basis, warp 1 = TMEM allocator +
+// single-thread MMA issuer, warp 2 lane 0 = producer of the x tiles, warps
+// 3-10 = converters (x tile -> FP16 [x_hi; x_lo] B operand, two group slots)
+// and epilogue (TMEM -> W; TMEM -> intermediate t1 [ny][R][K][pxp]); two
+// epilogue warps share each TMEM lane quarter and split the unit's right-hand
+// sides.  All waits are bounded; on timeout the kernel
+// records an error code, drains its own copies, frees TMEM and returns.
 
 #include "zl_internal.cuh"
 #include "tc_ptx.cuh"
@@ -47,7 +66,7 @@ namespace zl {
 
 struct TcOperands {
     __half* pimg = nullptr;    // [nh][128 rows][nwp] K-major image of [P_hi; P_lo] per column
-    uint8_t* bximg = nullptr;  // per 8-column group: [2 splits][2 chunks (same values)][6 row groups][128 B]
+    uint8_t* bximg = nullptr;  // per 8-column group: K-chunks [b_hi | b_hi | b_lo] x 6 row groups x 128 B
     int* d_err = nullptr;      // device error word (0 = ok)
     int nwp = 0;               // V1 K extent: n_w rounded up to 16 or 32
     int pxp = 0;               // row stride of t1 (Px rounded up to 4)
@@ -59,40 +78,46 @@ namespace {
 
 using namespace tc;
 
-constexpr int RC = 16;                 // right-hand sides per unit (V1 N)
-constexpr int GC = 8;                  // columns per group (one x-pass K-step: 8 columns x 2 halves)
+constexpr int RC = 16;                 // right-hand sides per unit
+constexpr int N1 = 2 * RC;             // V1 N: [x_hi; x_lo]
+constexpr int GC = 8;                  // columns per group (one x-pass K-chunk)
+constexpr int HG = 4;                  // columns per V1 half-group
 constexpr int N2 = 48;                 // x-pass N: kept x-frequencies padded
 constexpr int MT = 8;                  // x-pass M tiles: 64 members x 16 rhs / 128
-constexpr int SP = 13;                 // P image ring depth: more than a group, so a slot is
-                                       // requested about one group period before its use
+constexpr int SPH = 3;                 // P image ring depth in half-groups (4 images per slot)
 constexpr int SX = 2;                  // x tile ring depth
 constexpr int SB = 3;                  // x-pass basis ring depth
+static_assert(SB == SPH, "one completion wait covers an image slot and a basis stage");
 constexpr int NEPI = 8;                // epilogue / converter warps
 constexpr int kEpiWarp0 = 3;           // warps 0: P/basis producer, 1: MMA, 2: x producer
 constexpr int kThreadsTc = 32 * kEpiWarp0 + 32 * NEPI;
 constexpr int kEpiThreads = 32 * NEPI;
-constexpr uint32_t kD1Col = MT * N2;   // 384: D1 (V1 accumulators) after the x-pass accumulators
+constexpr uint32_t kD1Col = MT * N2;   // 384: V1 accumulators after the x-pass accumulators
 constexpr uint32_t kTmemCols = 512;
+static_assert(kD1Col + HG * N1 <= kTmemCols, "TMEM columns");
 constexpr uint32_t kWChunk = 16384;    // one K-chunk of W: 1024 rows x 16 B
-constexpr uint32_t kWSplit = 32768;    // hi / lo offset inside W
-constexpr uint32_t kBxStage = 3072;    // x-pass basis per group: 2 splits x 2 chunks x 6 row groups x 128 B
+constexpr uint32_t kWBytes = 3 * kWChunk;   // chunks: 0 = W_lo, 1 = W_hi, 2 = W_c
+constexpr uint32_t kBxChunk = 768;     // one K-chunk of the x-pass basis: 48 rows x 16 B
+constexpr uint32_t kBxStage = 3 * kBxChunk;   // chunks: b_hi, b_hi, b_lo
 constexpr unsigned long long kWaitCycles = 4000000000ull;   // ~2 s at 2 GHz
 
-// Barrier slots.  The MMA thread commits once per group for V1 and once for the x-pass,
-// each into a ring of kDone barriers (group gi -> slot gi % kDone): every consumer that must
-// know "V1 / x-pass of group g has completed" waits there, and kDone > the largest lag of
-// any waiter keeps the phase parity unambiguous.
-constexpr int kDone = 4;
+// Completion ring.  The MMA thread commits once per V1 half-group n (V1DONE, slot n % kDoneV);
+// the commit of half-group 2g + 1 also covers the x-pass of group g - 1, issued before it.
+// Every consumer that must know "V1 of half-group n (and everything issued earlier) has
+// completed" waits there; a waiter never lags the newest commit by a full ring (the producer
+// lags by at most two half-groups, the epilogue by at most one), so the phase parity is
+// unambiguous.  The x-pass of a CTA's last group, issued after its last V1, commits to XLAST.
+constexpr int kDoneV = 8;
 constexpr uint32_t kL2Ahead = 2;       // groups between an L2 prefetch and the shared-memory load
 enum {
     B_PFULL = 0,
-    B_XFULL = B_PFULL + SP,
+    B_XFULL = B_PFULL + SPH,
     B_XEMPTY = B_XFULL + SX,
     B_BXFULL = B_XEMPTY + SX,
     B_V1DONE = B_BXFULL + SB,
-    B_XDONE = B_V1DONE + kDone,
-    B_B1FULL = B_XDONE + kDone,
-    B_D1EMPTY,
+    B_XLAST = B_V1DONE + kDoneV,
+    B_B1FULL,                          // two slots: the B operand of group g lives in slot g % 2
+    B_D1EMPTY = B_B1FULL + 2,
     B_WFULL,
     B_D2EMPTY,
     B_FIN,
@@ -107,28 +132,31 @@ struct SmemPlan {
     uint32_t pring, xring, bxring, b1, w, bars, total;
 };
 
-__host__ __device__ inline uint32_t b1_stride(int nwp) { return 64u * nwp + 16u; }   // hi + lo + 16 B pad
+// B operand of one column: 32 rows ([x_hi; x_lo]) x nwp FP16, plus 16 bytes so that the
+// eight columns of a group fall in different banks
+__host__ __device__ constexpr uint32_t b1_stride(int nwp) { return 64u * nwp + 16u; }
 
-__host__ __device__ inline SmemPlan smem_plan(int nwp) {
-    SmemPlan s;
+__host__ __device__ constexpr SmemPlan smem_plan(int nwp) {
+    SmemPlan s{};
     uint32_t o = 0;
     s.pring = o;
-    o += SP * 256u * nwp;                // 128 rows x nwp x 2 B
+    o += SPH * HG * 256u * nwp;          // per slot: 4 images of 128 rows x nwp x 2 B
     s.xring = o;
     o += SX * 512u * nwp;                // RC x nwp x GC x 4 B
     s.bxring = o;
     o += SB * kBxStage;
+    o = (o + 127u) & ~127u;
     s.b1 = o;
-    o += GC * b1_stride(nwp);
+    o += 2 * GC * b1_stride(nwp);
     o = (o + 127u) & ~127u;
     s.w = o;
-    o += 2 * kWSplit;
+    o += kWBytes;
     s.bars = o;
     o += kBarBytes;
     s.total = o;
     return s;
 }
-
+static_assert(smem_plan(32).total <= 232448, "shared memory plan exceeds 227 KB");
 
 // Bounded wait.  The fast path (phase already complete) is one try_wait; the clock and the
 // abort flag are looked at only every 1024 polls, so waits cost the single-thread roles little.
@@ -163,6 +191,11 @@ __device__ __forceinline__ void split2(float a, float b, uint32_t& hi, uint32_t&
     lo = *reinterpret_cast<const uint32_t*>(&l);
 }
 
+__device__ __forceinline__ uint32_t pack_half2(float a, float b) {
+    const __half2 h = __floats2half2_rn(a, b);
+    return *reinterpret_cast<const uint32_t*>(&h);
+}
+
 // Bounded drain of a producer ring slot: wait for the last phase issued into it.
 __device__ __forceinline__ void drain_slot(uint64_t* bar, uint32_t issued, uint32_t slot, uint32_t depth) {
     if (issued <= slot) return;
@@ -178,7 +211,7 @@ fwd_column_tc_kernel(const __grid_constant__ CUtensorMap tmap_x, const __half* _
                      int R, int K, int nx, int ny, int pxp) {
     constexpr int nwp = NWP;
     extern __shared__ __align__(1024) uint8_t smem[];
-    const SmemPlan sp = smem_plan(nwp);
+    constexpr SmemPlan sp = smem_plan(NWP);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + sp.bars);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + B_COUNT);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
@@ -192,26 +225,27 @@ fwd_column_tc_kernel(const __grid_constant__ CUtensorMap tmap_x, const __half* _
     const int n_rc = (R + RC - 1) / RC;
     const int units = ny * n_rc;
     const int G = nx / GC;
-    // units of this CTA: blockIdx.x + i * gridDim.x; groups are numbered across them
+    // units of this CTA: blockIdx.x + i * gridDim.x; groups (and half-groups) are numbered across them
     const int my_units = blockIdx.x < units ? (units - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     const uint32_t total_groups = (uint32_t)my_units * (uint32_t)G;
     constexpr uint32_t PBYTES = 256u * NWP;
+    constexpr uint32_t PSLOT = HG * PBYTES;
     constexpr uint32_t XBYTES = 512u * NWP;
-    constexpr uint32_t B1S = 64u * NWP + 16u;
+    constexpr uint32_t B1S = b1_stride(NWP);
+    constexpr uint32_t B1SLOT = GC * B1S;
     constexpr uint32_t b1_sbo = (uint32_t)(NWP / 8) * 128u;
 
     if (tid == 0) {
-        for (int i = 0; i < SP; ++i) mbar_init(&bars[B_PFULL + i], 1);
+        for (int i = 0; i < SPH; ++i) mbar_init(&bars[B_PFULL + i], 1);
         for (int i = 0; i < SX; ++i) {
             mbar_init(&bars[B_XFULL + i], 1);
             mbar_init(&bars[B_XEMPTY + i], kEpiThreads);
         }
         for (int i = 0; i < SB; ++i) mbar_init(&bars[B_BXFULL + i], 1);
-        for (int i = 0; i < kDone; ++i) {
-            mbar_init(&bars[B_V1DONE + i], 1);
-            mbar_init(&bars[B_XDONE + i], 1);
-        }
+        for (int i = 0; i < kDoneV; ++i) mbar_init(&bars[B_V1DONE + i], 1);
+        mbar_init(&bars[B_XLAST], 1);
         mbar_init(&bars[B_B1FULL], kEpiThreads);
+        mbar_init(&bars[B_B1FULL + 1], kEpiThreads);
         mbar_init(&bars[B_D1EMPTY], kEpiThreads);
         mbar_init(&bars[B_WFULL], kEpiThreads);
         mbar_init(&bars[B_D2EMPTY], kEpiThreads);
@@ -227,45 +261,41 @@ fwd_column_tc_kernel(const __grid_constant__ CUtensorMap tmap_x, const __half* _
     const uint32_t tbase = *tslot;
 
     if (warp == 0) {
-        // ------------------------------------------------------------ producer: basis + P images
+        // ------------------------------------------------------------ producer: images + x-pass basis
         if (lane == 0) {
-            uint32_t pc = 0, bc = 0;
-            bool ok = true;
-            for (uint32_t gi = 0; gi < total_groups && ok; ++gi) {
+            uint32_t pc = 0, bc = 0;           // half-groups, basis stages issued
+            for (uint32_t n = 0; n < 2 * total_groups; ++n) {
+                const uint32_t gi = n >> 1;
                 const int u = (int)blockIdx.x + (int)(gi / G) * (int)gridDim.x;
-                const int g = (int)(gi % G);
                 const int y = u / n_rc;
-                // basis stage gi % SB was last used by the x-pass of group gi - SB
-                const uint32_t bs = bc % SB;
-                if (bc >= SB) {
-                    const uint32_t gp = bc - SB;
-                    if (!wait_bar(&bars[B_XDONE + gp % kDone], (gp / kDone) & 1u, abort_flag)) { fail(abort_flag, err, 1); ok = false; break; }
+                // image slot n % SPH was last used by V1 of half-group n - SPH; for even n = 2gi the
+                // same commit covers the x-pass of group gi - SB (SB == SPH), the last user of the
+                // basis stage gi % SB
+                const uint32_t ps = n % SPH;
+                if (n >= SPH) {
+                    const uint32_t np = n - SPH;
+                    if (!wait_bar(&bars[B_V1DONE + np % kDoneV], (np / kDoneV) & 1u, abort_flag)) { fail(abort_flag, err, 1); break; }
                 }
-                mbar_arrive_expect_tx(&bars[B_BXFULL + bs], kBxStage);
-                bulk_g2s(sbxring + bs * kBxStage, bximg + (size_t)g * kBxStage, kBxStage, &bars[B_BXFULL + bs]);
-                ++bc;
-                for (int j = 0; j < GC; ++j) {
-                    // image slot pc % SP was last used by load pc - SP, i.e. by V1 of group (pc - SP) / GC
-                    const uint32_t ps = pc % SP;
-                    if (pc >= SP) {
-                        const uint32_t gp = (pc - SP) / GC;
-                        if (!wait_bar(&bars[B_V1DONE + gp % kDone], (gp / kDone) & 1u, abort_flag)) { fail(abort_flag, err, 1); ok = false; break; }
-                    }
-                    mbar_arrive_expect_tx(&bars[B_PFULL + ps], PBYTES);
-                    const size_t col = (size_t)y * nx + (size_t)g * GC + j;
-                    bulk_g2s(spring + ps * PBYTES, pimg + col * 128u * nwp, PBYTES, &bars[B_PFULL + ps]);
-                    ++pc;
-                    // warm L2 with the image this CTA loads two groups later
-                    const uint32_t ga = gi + kL2Ahead;
-                    if (ga < total_groups) {
-                        const int ua = (int)blockIdx.x + (int)(ga / G) * (int)gridDim.x;
-                        const size_t cola = (size_t)(ua / n_rc) * nx + (size_t)(ga % G) * GC + j;
-                        prefetch_l2(pimg + cola * 128u * nwp, PBYTES);
-                    }
+                if ((n & 1u) == 0) {
+                    const uint32_t bs = bc % SB;
+                    mbar_arrive_expect_tx(&bars[B_BXFULL + bs], kBxStage);
+                    bulk_g2s(sbxring + bs * kBxStage, bximg + (size_t)(gi % G) * kBxStage, kBxStage, &bars[B_BXFULL + bs]);
+                    ++bc;
+                }
+                mbar_arrive_expect_tx(&bars[B_PFULL + ps], PSLOT);
+                const size_t col = (size_t)y * nx + (size_t)(gi % G) * GC + (n & 1u) * HG;
+                bulk_g2s(spring + ps * PSLOT, pimg + col * 128u * nwp, PSLOT, &bars[B_PFULL + ps]);
+                ++pc;
+                // warm L2 with the eight images of the group this CTA reaches two groups later
+                const uint32_t ga = gi + kL2Ahead;
+                if ((n & 1u) == 0 && ga < total_groups) {
+                    const int ua = (int)blockIdx.x + (int)(ga / G) * (int)gridDim.x;
+                    const size_t cola = (size_t)(ua / n_rc) * nx + (size_t)(ga % G) * GC;
+                    prefetch_l2(pimg + cola * 128u * nwp, GC * PBYTES);
                 }
             }
             // every issued copy must land before the CTA exits
-            for (uint32_t s = 0; s < SP; ++s) drain_slot(&bars[B_PFULL + s], pc, s, SP);
+            for (uint32_t s = 0; s < SPH; ++s) drain_slot(&bars[B_PFULL + s], pc, s, SPH);
             for (uint32_t s = 0; s < SB; ++s) drain_slot(&bars[B_BXFULL + s], bc, s, SB);
         }
     } else if (warp == 2) {
@@ -292,7 +322,7 @@ fwd_column_tc_kernel(const __grid_constant__ CUtensorMap tmap_x, const __half* _
     } else if (warp == 1) {
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
-            constexpr uint32_t idesc_v1 = idesc_f16_f32(128, RC);
+            constexpr uint32_t idesc_v1 = idesc_f16_f32(128, N1);
             constexpr uint32_t idesc_x = idesc_f16_f32(128, N2);
             constexpr uint32_t a_sbo = (uint32_t)(NWP / 8) * 128u;
             // Base descriptors: an operand b bytes further on is the base plus (b >> 4) in the
@@ -300,166 +330,202 @@ fwd_column_tc_kernel(const __grid_constant__ CUtensorMap tmap_x, const __half* _
             const uint64_t dA0 = smem_desc(smem_u32(spring), 128u, a_sbo);
             const uint64_t dB0 = smem_desc(smem_u32(sb1), 128u, b1_sbo);
             const uint64_t dW0 = smem_desc(smem_u32(sw), kWChunk, 128u);
-            const uint64_t dX0 = smem_desc(smem_u32(sbxring), 768u, 128u);
-            uint32_t pc = 0;
+            const uint64_t dX0 = smem_desc(smem_u32(sbxring), kBxChunk, 128u);
             bool ok = true;
-            // x-pass of group gi (W and basis stage of gi ready); first of a unit overwrites D2
-            auto xpass = [&](uint32_t gi) -> bool {
-                const uint32_t bs = gi % SB, bph = (gi / SB) & 1u;
-                if (!wait_bar(&bars[B_WFULL], gi & 1u, abort_flag)) return false;
-                if (!wait_bar(&bars[B_BXFULL + bs], bph, abort_flag)) return false;
-                const bool first = (gi % G) == 0;
-                if (first && !wait_bar(&bars[B_D2EMPTY], ((gi / G) & 1u) ^ 1u, abort_flag)) return false;
+            // V1 of half-group n (columns 4(n % 2) .. +3 of group n / 2) into the D1 columns
+            auto v1 = [&](uint32_t n) -> bool {
+                const uint32_t g = n >> 1, h = n & 1u;
+                if (!wait_bar(&bars[B_B1FULL + (g & 1u)], (g >> 1) & 1u, abort_flag)) return false;
+                if (!wait_bar(&bars[B_D1EMPTY], (n & 1u) ^ 1u, abort_flag)) return false;
                 tc_fence_after();
-                const uint64_t dbhi = dX0 + ((bs * kBxStage) >> 4);
-                const uint64_t dblo = dbhi + ((kBxStage / 2) >> 4);
-                const uint32_t acc0 = first ? 0u : 1u;
-                // product-major across the eight row tiles (independent accumulators back to back)
+                const uint64_t db = dB0 + (((g & 1u) * B1SLOT + h * HG * B1S) >> 4);
+                const uint32_t ps = n % SPH;
+                if (!wait_bar(&bars[B_PFULL + ps], (n / SPH) & 1u, abort_flag)) return false;
+                tc_fence_after();
 #pragma unroll
-                for (int t = 0; t < MT; ++t) mma_f16(tbase + (uint32_t)(t * N2), dW0 + ((t * 2048u) >> 4), dbhi, idesc_x, acc0);
+                for (int j = 0; j < HG; ++j) {
+                    const uint64_t da = dA0 + ((ps * PSLOT + (uint32_t)j * PBYTES) >> 4);
 #pragma unroll
-                for (int t = 0; t < MT; ++t)
-                    mma_f16(tbase + (uint32_t)(t * N2), dW0 + ((kWSplit + t * 2048u) >> 4), dbhi, idesc_x, 1u);
-#pragma unroll
-                for (int t = 0; t < MT; ++t) mma_f16(tbase + (uint32_t)(t * N2), dW0 + ((t * 2048u) >> 4), dblo, idesc_x, 1u);
-                mma_commit(&bars[B_XDONE + gi % kDone]);   // W, the basis stage and (last group) D2
+                    for (int ks = 0; ks < NWP / 16; ++ks)
+                        mma_f16(tbase + kD1Col + (uint32_t)(j * N1), da + (uint64_t)(ks * 16),
+                                db + (uint64_t)((j * B1S + ks * 256u) >> 4), idesc_v1, ks > 0 ? 1u : 0u);
+                }
+                mma_commit(&bars[B_V1DONE + n % kDoneV]);   // D1, B1, the image slot (+ the x-pass before it)
                 return true;
             };
-            for (uint32_t gi = 0; gi < total_groups && ok; ++gi) {
-                if (!wait_bar(&bars[B_B1FULL], gi & 1u, abort_flag) ||
-                    !wait_bar(&bars[B_D1EMPTY], (gi & 1u) ^ 1u, abort_flag)) { fail(abort_flag, err, 2); ok = false; break; }
-                // column by column: each column's four MMAs start as soon as its image has landed
+            // x-pass of group gi (W, the basis stage and, first group of a unit, the drained D2)
+            auto xpass = [&](uint32_t gi) -> bool {
+                const uint32_t bs = gi % SB, bph = (gi / SB) & 1u;
+                const bool first = (gi % G) == 0;
+                if (!wait_bar(&bars[B_WFULL], gi & 1u, abort_flag)) return false;
+                if (!wait_bar(&bars[B_BXFULL + bs], bph, abort_flag)) return false;
+                if (first && !wait_bar(&bars[B_D2EMPTY], ((gi / G) & 1u) ^ 1u, abort_flag)) return false;
                 tc_fence_after();
+                const uint64_t db0 = dX0 + ((bs * kBxStage) >> 4);   // K-chunks [b_hi | b_hi]
+                const uint64_t db1 = db0 + (kBxChunk >> 4);          // K-chunks [b_hi | b_lo]
+                const uint64_t dw0 = dW0 + (kWChunk >> 4);           // K-chunks [W_hi | W_c]
+                const uint64_t dw1 = dW0;                            // K-chunks [W_lo | W_hi]
+                const uint32_t acc0 = first ? 0u : 1u;
 #pragma unroll
-                for (int j = 0; j < GC; ++j) {
-                    const uint32_t ps = (pc + j) % SP, pph = ((pc + j) / SP) & 1u;
-                    if (!wait_bar(&bars[B_PFULL + ps], pph, abort_flag)) { fail(abort_flag, err, 2); ok = false; break; }
-                    tc_fence_after();
-                    const uint64_t da = dA0 + ((ps * PBYTES) >> 4);
+                for (int t = 0; t < MT; ++t) mma_f16(tbase + (uint32_t)(t * N2), dw0 + ((t * 2048u) >> 4), db0, idesc_x, acc0);
 #pragma unroll
-                    for (int half = 0; half < 2; ++half)             // B = x_hi, then x_lo
-#pragma unroll
-                        for (int ks = 0; ks < NWP / 16; ++ks)
-                            mma_f16(tbase + kD1Col + (uint32_t)(j * RC), da + (uint64_t)(ks * 16),
-                                    dB0 + (uint64_t)((j * B1S + half * 32u * NWP + ks * 256u) >> 4), idesc_v1,
-                                    (half | ks) ? 1u : 0u);
-                }
-                if (!ok) break;
-                pc += GC;
-                mma_commit(&bars[B_V1DONE + gi % kDone]);   // D1, B1 and the group's eight image slots
-                if (gi > 0 && !xpass(gi - 1)) { fail(abort_flag, err, 2); ok = false; break; }
+                for (int t = 0; t < MT; ++t) mma_f16(tbase + (uint32_t)(t * N2), dw1 + ((t * 2048u) >> 4), db1, idesc_x, 1u);
+                return true;
+            };
+            for (uint32_t gi = 0; gi < total_groups && ok; ++gi)
+                ok = v1(2 * gi) && (gi == 0 || xpass(gi - 1)) && v1(2 * gi + 1);
+            if (ok && total_groups > 0) {
+                ok = xpass(total_groups - 1);
+                if (ok) mma_commit(&bars[B_XLAST]);
             }
-            if (ok && total_groups > 0 && !xpass(total_groups - 1)) fail(abort_flag, err, 2);
+            if (!ok) fail(abort_flag, err, 2);
             mma_commit(&bars[B_FIN]);
             const long long t0 = clock64();
             while (!mbar_try_wait(&bars[B_FIN], 0) && (unsigned long long)(clock64() - t0) < kWaitCycles) {}
         }
     } else {
         // ------------------------------------------------------------ converters + epilogue
-        const int et = tid - 32 * kEpiWarp0;           // 0 .. kEpiThreads-1
+        const int ew = warp - kEpiWarp0;               // 0 .. NEPI-1
         const int q = warp & 3;                        // TMEM lane quarter this warp may access
-        const int rset = (warp - kEpiWarp0) >> 2;      // rhs half of the unit this warp finalises
+        const int rset = ew >> 2;                      // rhs half of the unit this warp finalises
         const uint32_t lane_off = (uint32_t)(32 * q) << 16;
         const int kk = (q & 1) * 32 + lane;            // member of this thread's TMEM lane
-        const uint32_t half_chunk = q < 2 ? 0u : kWChunk;   // P_hi x -> K-chunk 0, P_lo x -> K-chunk 1
-        uint32_t conv = 0;
+        const bool hi_part = q < 2;                    // lanes < 64: P_hi x, lanes >= 64: P_lo x
         bool ok = true;
 
+        // x tile of group c ([RC][nwp][GC] FP32) -> B operand slot c % 2: per column, rows
+        // 0..15 = x_hi, 16..31 = x_lo.  A warp handles one (rhs, octet of levels) per step:
+        // lane (il, j) reads levels il and il + 4 of column j (conflict-free: 32 distinct
+        // banks), one shuffle pairs neighbouring levels, and each lane stores one 4-byte
+        // pair of x_hi and one of x_lo (banks 4j + pair: conflict-free).
         auto convert = [&](uint32_t c) -> bool {
             const uint32_t xs = c % SX, xph = (c / SX) & 1u;
             if (!warp_wait_bar(&bars[B_XFULL + xs], xph, abort_flag)) return false;
-            // B1 is free: the caller has seen V1 of group c - 1 complete
-            const float* xt = reinterpret_cast<const float*>(sxring + xs * XBYTES);   // [RC][nwp][GC]
-            uint8_t* b1 = sb1;
-            const int noct = nwp / 8;
-            for (int item = et; item < GC * RC * noct; item += kEpiThreads) {
-                const int j = item % GC, rest = item / GC;
-                const int o = rest % noct, r = rest / noct;
-                float v[8];
-#pragma unroll
-                for (int i = 0; i < 8; ++i) v[i] = xt[(r * nwp + 8 * o + i) * GC + j];
-                uint4 hi, lo;
-                split2(v[0], v[1], hi.x, lo.x);
-                split2(v[2], v[3], hi.y, lo.y);
-                split2(v[4], v[5], hi.z, lo.z);
-                split2(v[6], v[7], hi.w, lo.w);
-                uint8_t* dst = b1 + j * B1S + (r >> 3) * b1_sbo + o * 128u + (r & 7) * 16u;
-                *reinterpret_cast<uint4*>(dst) = hi;
-                *reinterpret_cast<uint4*>(dst + 32u * nwp) = lo;
+            const float* xt = reinterpret_cast<const float*>(sxring + xs * XBYTES);
+            uint8_t* b1 = sb1 + (c & 1u) * B1SLOT;
+            const int il = lane >> 3, j = lane & 7;
+            const bool odd = (il & 1) != 0;
+            const int l0 = odd ? il + 3 : il;          // first level of this lane's pair in the octet
+#pragma unroll 2
+            for (int it = ew; it < RC * (NWP / 8); it += NEPI) {
+                const int r = it / (NWP / 8), o = it % (NWP / 8);
+                const float* src = xt + (r * NWP + 8 * o) * GC + j;
+                const float a = src[il * GC];
+                const float b = src[(il + 4) * GC];
+                const float recv = __shfl_xor_sync(0xffffffffu, odd ? a : b, 8);
+                uint32_t hi, lo;
+                split2(odd ? recv : a, odd ? b : recv, hi, lo);
+                uint8_t* dst = b1 + j * B1S + (r >> 3) * b1_sbo + o * 128u + (r & 7) * 16u + l0 * 2u;
+                *reinterpret_cast<uint32_t*>(dst) = hi;
+                *reinterpret_cast<uint32_t*>(dst + 32u * NWP) = lo;   // rows 16..31
             }
             fence_proxy_async_smem();
-            mbar_arrive(&bars[B_B1FULL]);
+            mbar_arrive(&bars[B_B1FULL + (c & 1u)]);
             mbar_arrive(&bars[B_XEMPTY + xs]);
             return true;
         };
 
-        if (total_groups > 0) {
-            if (!convert(0)) { fail(abort_flag, err, 3); ok = false; }
-            conv = 1;
-        }
-        for (uint32_t gi = 0; gi < total_groups && ok; ++gi) {
-            const int u = (int)blockIdx.x + (int)(gi / G) * (int)gridDim.x;
+        // D2 of a finished unit (its last x-pass has completed): rows (r, k) -> t1[y][r0 + r][k][0..pxp)
+        auto drain_d2 = [&](uint32_t gl) -> bool {
+            const int u = (int)blockIdx.x + (int)(gl / G) * (int)gridDim.x;
             const int y = u / n_rc, r0 = (u % n_rc) * RC;
-            // ---- D1 of group gi: 8 columns x 8 rhs of this thread's lane
-            if (!warp_wait_bar(&bars[B_V1DONE + gi % kDone], (gi / kDone) & 1u, abort_flag)) { fail(abort_flag, err, 3); ok = false; break; }
             tc_fence_after();
-            uint32_t v[GC][8];
+#pragma unroll 1
+            for (int t = rset; t < MT; t += 2) {
+                const int row = 128 * t + 32 * q + lane;
+                const int r = row >> 6, k = row & 63;
+                uint32_t dv[N2];
+                tmem_ld16(tbase + lane_off + (uint32_t)(t * N2), *reinterpret_cast<uint32_t(*)[16]>(&dv[0]));
+                tmem_ld16(tbase + lane_off + (uint32_t)(t * N2 + 16), *reinterpret_cast<uint32_t(*)[16]>(&dv[16]));
+                tmem_ld16(tbase + lane_off + (uint32_t)(t * N2 + 32), *reinterpret_cast<uint32_t(*)[16]>(&dv[32]));
+                tmem_ld_wait();
+                if (r0 + r < R && k < K) {
+                    float4* dst = reinterpret_cast<float4*>(t1 + (((size_t)y * R + r0 + r) * K + k) * pxp);
 #pragma unroll
-            for (int j = 0; j < GC; ++j) tmem_ld8(tbase + lane_off + kD1Col + (uint32_t)(j * RC + rset * 8), v[j]);
+                    for (int c = 0; c < N2 / 4; ++c)
+                        if (4 * c < pxp)
+                            dst[c] = make_float4(__uint_as_float(dv[4 * c]), __uint_as_float(dv[4 * c + 1]),
+                                                 __uint_as_float(dv[4 * c + 2]), __uint_as_float(dv[4 * c + 3]));
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(&bars[B_D2EMPTY]);
+            return true;
+        };
+
+        if (total_groups > 0 && !convert(0)) ok = false;
+        if (ok && total_groups > 1 && !convert(1)) ok = false;
+        float s[GC][8];                                // w of this lane: column x rhs (8 of the unit's 16)
+        bool pending = false;                          // a finished unit whose D2 is still to be drained
+        uint32_t pending_g = 0;
+        for (uint32_t n = 0; n < 2 * total_groups && ok; ++n) {
+            const uint32_t g = n >> 1, h = n & 1u;
+            // ---- D1 of half-group n: 4 columns x (8 rhs x_hi products, 8 rhs x_lo products)
+            if (!warp_wait_bar(&bars[B_V1DONE + n % kDoneV], (n / kDoneV) & 1u, abort_flag)) { ok = false; break; }
+            tc_fence_after();
+            uint32_t v[HG][16];
+#pragma unroll
+            for (int j = 0; j < HG; ++j) {
+                tmem_ld8(tbase + lane_off + kD1Col + (uint32_t)(j * N1 + rset * 8), *reinterpret_cast<uint32_t(*)[8]>(&v[j][0]));
+                tmem_ld8(tbase + lane_off + kD1Col + (uint32_t)(j * N1 + RC + rset * 8), *reinterpret_cast<uint32_t(*)[8]>(&v[j][8]));
+            }
             tmem_ld_wait();
             tc_fence_before();
             mbar_arrive(&bars[B_D1EMPTY]);
-            // ---- the MMA needs group gi+1's x operand next: convert it before the W write
-            if (conv < total_groups) {
-                if (!convert(conv)) { fail(abort_flag, err, 3); ok = false; break; }
-                ++conv;
-            }
-            uint4 hi[8], lo[8];
+            // (two branches keep every index of s a compile-time constant: s stays in registers)
+            if (h == 0) {
 #pragma unroll
-            for (int rl = 0; rl < 8; ++rl) {
-                split2(__uint_as_float(v[0][rl]), __uint_as_float(v[1][rl]), hi[rl].x, lo[rl].x);
-                split2(__uint_as_float(v[2][rl]), __uint_as_float(v[3][rl]), hi[rl].y, lo[rl].y);
-                split2(__uint_as_float(v[4][rl]), __uint_as_float(v[5][rl]), hi[rl].z, lo[rl].z);
-                split2(__uint_as_float(v[6][rl]), __uint_as_float(v[7][rl]), hi[rl].w, lo[rl].w);
+                for (int j = 0; j < HG; ++j)
+#pragma unroll
+                    for (int rl = 0; rl < 8; ++rl) s[j][rl] = __uint_as_float(v[j][rl]) + __uint_as_float(v[j][8 + rl]);
+            } else {
+#pragma unroll
+                for (int j = 0; j < HG; ++j)
+#pragma unroll
+                    for (int rl = 0; rl < 8; ++rl) s[HG + j][rl] = __uint_as_float(v[j][rl]) + __uint_as_float(v[j][8 + rl]);
             }
-            // ---- W: rows (r, k), K-chunk = half (P_hi x or P_lo x), 8 columns per 16-byte row
-            // W is free once the x-pass of the previous group has completed
-            if (gi > 0 && !warp_wait_bar(&bars[B_XDONE + (gi - 1) % kDone], ((gi - 1) / kDone) & 1u, abort_flag)) { fail(abort_flag, err, 3); ok = false; break; }
+            if (h == 0) {
+                // V1 of group g - 1 has completed, so its B operand slot takes group g + 1; the
+                // MMA thread needs that slot a whole group later, while D1 is needed right away
+                if (g >= 1 && g + 1 < total_groups && !convert(g + 1)) { ok = false; break; }
+                continue;
+            }
+            // ---- the commit just seen covers the x-pass of group g - 1: W is free, and a unit that
+            // ended at group g - 1 has its whole row in D2
+            if (pending) {
+                if (!drain_d2(pending_g)) { ok = false; break; }
+                pending = false;
+            }
+            // ---- W of group g: rows (r, k), 8 columns per 16-byte row in each K-chunk
 #pragma unroll
             for (int rl = 0; rl < 8; ++rl) {
                 const uint32_t row = (uint32_t)(rset * 8 + rl) * 64u + (uint32_t)kk;
-                const uint32_t off = half_chunk + (row >> 3) * 128u + (row & 7u) * 16u;
-                *reinterpret_cast<uint4*>(sw + off) = hi[rl];
-                *reinterpret_cast<uint4*>(sw + kWSplit + off) = lo[rl];
+                const uint32_t off = (row >> 3) * 128u + (row & 7u) * 16u;
+                if (hi_part) {
+                    uint4 hi, lo;
+                    split2(s[0][rl], s[1][rl], hi.x, lo.x);
+                    split2(s[2][rl], s[3][rl], hi.y, lo.y);
+                    split2(s[4][rl], s[5][rl], hi.z, lo.z);
+                    split2(s[6][rl], s[7][rl], hi.w, lo.w);
+                    *reinterpret_cast<uint4*>(sw + kWChunk + off) = hi;   // W_hi
+                    *reinterpret_cast<uint4*>(sw + off) = lo;             // W_lo
+                } else {
+                    const uint4 c = make_uint4(pack_half2(s[0][rl], s[1][rl]), pack_half2(s[2][rl], s[3][rl]),
+                                               pack_half2(s[4][rl], s[5][rl]), pack_half2(s[6][rl], s[7][rl]));
+                    *reinterpret_cast<uint4*>(sw + 2 * kWChunk + off) = c;   // W_c
+                }
             }
             fence_proxy_async_smem();
             mbar_arrive(&bars[B_WFULL]);
-            // ---- end of a unit: D2 holds the row's x-pass, rows (r, k) -> t1[y][r0 + r][k][0..pxp)
-            if ((gi % G) == (uint32_t)G - 1) {
-                if (!warp_wait_bar(&bars[B_XDONE + gi % kDone], (gi / kDone) & 1u, abort_flag)) { fail(abort_flag, err, 3); ok = false; break; }
-                tc_fence_after();
-#pragma unroll 1
-                for (int t = rset; t < MT; t += 2) {
-                    const int row = 128 * t + 32 * q + lane;
-                    const int r = row >> 6, k = row & 63;
-                    uint32_t dv[N2];
-                    tmem_ld16(tbase + lane_off + (uint32_t)(t * N2), *reinterpret_cast<uint32_t(*)[16]>(&dv[0]));
-                    tmem_ld16(tbase + lane_off + (uint32_t)(t * N2 + 16), *reinterpret_cast<uint32_t(*)[16]>(&dv[16]));
-                    tmem_ld16(tbase + lane_off + (uint32_t)(t * N2 + 32), *reinterpret_cast<uint32_t(*)[16]>(&dv[32]));
-                    tmem_ld_wait();
-                    if (r0 + r < R && k < K) {
-                        float4* dst = reinterpret_cast<float4*>(t1 + (((size_t)y * R + r0 + r) * K + k) * pxp);
-#pragma unroll
-                        for (int c = 0; c < N2 / 4; ++c)
-                            if (4 * c < pxp)
-                                dst[c] = make_float4(__uint_as_float(dv[4 * c]), __uint_as_float(dv[4 * c + 1]),
-                                                     __uint_as_float(dv[4 * c + 2]), __uint_as_float(dv[4 * c + 3]));
-                    }
-                }
-                tc_fence_before();
-                mbar_arrive(&bars[B_D2EMPTY]);
+            if ((g % G) == (uint32_t)G - 1) {
+                pending = true;
+                pending_g = g;
             }
         }
+        if (ok && pending) {
+            if (!warp_wait_bar(&bars[B_XLAST], 0, abort_flag) || !drain_d2(pending_g)) ok = false;
+        }
+        if (!ok) fail(abort_flag, err, 3);
     }
 
     tc_fence_before();
@@ -550,21 +616,20 @@ zl_status tc_prepare(zl_plan_s& p, cudaStream_t s) {
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) {
-        // x-pass basis image, one stage per 8-column group g: B[jx][(h, m)] = b_{p_x}(8g + m) for both
-        // halves h (the K-chunk h of W holds P_hi x for h = 0 and P_lo x for h = 1); rows jx >= Px are 0
+        // x-pass basis image, one stage per 8-column group g: K-chunk c holds
+        // B[jx][m] = b_{p_x}(8g + m), split hi (chunks 0 and 1) / lo (chunk 2); rows jx >= Px are 0
         std::vector<__half> img(bx_bytes / 2, __float2half_rn(0.f));
         for (int g = 0; g < nx / GC; ++g)
-            for (int split = 0; split < 2; ++split)
-                for (int h = 0; h < 2; ++h)
-                    for (int jx = 0; jx < p.Px; ++jx)
-                        for (int m = 0; m < GC; ++m) {
-                            const double b = basis_value_d(nx, p.xfreq[jx], g * GC + m);
-                            const __half hi = __double2half(b);
-                            const __half v = split == 0 ? hi : __double2half(b - (double)__half2float(hi));
-                            const size_t off = (size_t)g * kBxStage + (size_t)split * (kBxStage / 2) +
-                                               kmajor_offset((uint32_t)jx, (uint32_t)(h * GC + m), 768u, 128u);
-                            img[off / 2] = v;
-                        }
+            for (int c = 0; c < 3; ++c)
+                for (int jx = 0; jx < p.Px; ++jx)
+                    for (int m = 0; m < GC; ++m) {
+                        const double b = basis_value_d(nx, p.xfreq[jx], g * GC + m);
+                        const __half hi = __double2half(b);
+                        const __half v = c < 2 ? hi : __double2half(b - (double)__half2float(hi));
+                        const size_t off = (size_t)g * kBxStage +
+                                           kmajor_offset((uint32_t)jx, (uint32_t)(c * GC + m), kBxChunk, 128u);
+                        img[off / 2] = v;
+                    }
         e = cudaMemcpyAsync(t->bximg, img.data(), bx_bytes, cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     }
