@@ -317,7 +317,11 @@ fwd_ypass_gemm(const T* __restrict__ t1, const T* __restrict__ byk, const int* _
 // FP32 y-pass with the t1 rows of the CTA's pairs and the kept y-basis rows streamed
 // through double-buffered shared memory by cp.async (16-byte copies), so that enough
 // bytes are in flight to run at memory speed.  Needs ldp % 4 == 0 (16-byte rows).
-constexpr int kYAsync = 32;
+// Each thread accumulates two adjacent x-frequencies of one (rhs, member) pair for all
+// kept y-frequencies: one 8-byte load of t1 and PYT/4 broadcast 16-byte loads of the
+// y-basis feed 2 PYT FMAs, so the loop is bound by the FMA pipes rather than by the
+// shared-memory load pipe.  The output staging reuses the stream's shared memory.
+constexpr int kYAsync = 16;
 
 __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
@@ -336,9 +340,10 @@ fwd_ypass_async(const float* __restrict__ t1, const float* __restrict__ byk, con
     const int pw = ppc * ldp;                                   // floats of one y-row of this CTA
     float* st = reinterpret_cast<float*>(smem_raw);             // [2][kYAsync][pw]
     float* sb = st + 2 * kYAsync * pw;                          // [2][kYAsync][PYT]
-    float* sout = sb + 2 * kYAsync * PYT;                       // [ppc][PYT][Px]
+    float* sout = st;                                           // [ppc][PYT][Px], after the stream
     const int tid = threadIdx.x;
-    const int pl = tid / Px, jx = tid - pl * Px;
+    const int half = ldp / 2;                                   // threads per pair
+    const int pl = tid / half, jx = 2 * (tid - pl * half);      // columns jx, jx + 1
     const long long pair0 = (long long)blockIdx.x * ppc;
     const int npl = (int)min((long long)ppc, npairs - pair0);  // pairs this CTA really has
     const bool active = pl < npl;
@@ -360,9 +365,9 @@ fwd_ypass_async(const float* __restrict__ t1, const float* __restrict__ byk, con
         }
         cp_async_commit();
     };
-    float acc[PYT];
+    float acc0[PYT], acc1[PYT];
 #pragma unroll
-    for (int i = 0; i < PYT; ++i) acc[i] = 0.f;
+    for (int i = 0; i < PYT; ++i) acc0[i] = acc1[i] = 0.f;
     issue(0);
     for (int c = 0; c < nchunk; ++c) {
         if (c + 1 < nchunk) {
@@ -377,10 +382,20 @@ fwd_ypass_async(const float* __restrict__ t1, const float* __restrict__ byk, con
         const float* bb = sb + (c & 1) * kYAsync * PYT;
         if (active) {
             for (int yy = 0; yy < yn; ++yy) {
-                const float tv = tt[yy * pw];
-                const float* b = bb + yy * PYT;
+                const float2 tv = *reinterpret_cast<const float2*>(tt + yy * pw);
+                const float4* b = reinterpret_cast<const float4*>(bb + yy * PYT);
 #pragma unroll
-                for (int i = 0; i < PYT; ++i) acc[i] = fmaf(b[i], tv, acc[i]);
+                for (int i = 0; i < PYT / 4; ++i) {
+                    const float4 bv = b[i];
+                    acc0[4 * i] = fmaf(bv.x, tv.x, acc0[4 * i]);
+                    acc1[4 * i] = fmaf(bv.x, tv.y, acc1[4 * i]);
+                    acc0[4 * i + 1] = fmaf(bv.y, tv.x, acc0[4 * i + 1]);
+                    acc1[4 * i + 1] = fmaf(bv.y, tv.y, acc1[4 * i + 1]);
+                    acc0[4 * i + 2] = fmaf(bv.z, tv.x, acc0[4 * i + 2]);
+                    acc1[4 * i + 2] = fmaf(bv.z, tv.y, acc1[4 * i + 2]);
+                    acc0[4 * i + 3] = fmaf(bv.w, tv.x, acc0[4 * i + 3]);
+                    acc1[4 * i + 3] = fmaf(bv.w, tv.y, acc1[4 * i + 3]);
+                }
             }
         }
         __syncthreads();   // the buffer of chunk c is refilled by issue(c + 2)
@@ -388,7 +403,10 @@ fwd_ypass_async(const float* __restrict__ t1, const float* __restrict__ byk, con
     if (active) {
         float* so = sout + (size_t)pl * PYT * Px;
 #pragma unroll
-        for (int i = 0; i < PYT; ++i) so[i * Px + jx] = acc[i];
+        for (int i = 0; i < PYT; ++i) {
+            if (jx < Px) so[i * Px + jx] = acc0[i];
+            if (jx + 1 < Px) so[i * Px + jx + 1] = acc1[i];
+        }
     }
     __syncthreads();
     for (int pp = 0; pp < npl; ++pp) {
@@ -402,8 +420,9 @@ template <int PYT>
 cudaError_t launch_ypass_async(const zl_plan_s& p, const float* t1, int ldp, const float* byk, const int* m_ipy,
                                const int* m_jx, const float* scale, float* out, int R, cudaStream_t s) {
     const int npairs = R * p.d.K;
-    const int ppc = kThreads / p.Px;
-    const size_t smem = ((size_t)2 * kYAsync * ppc * ldp + 2 * kYAsync * PYT + (size_t)ppc * PYT * p.Px) * sizeof(float);
+    const int ppc = kThreads / (ldp / 2);                       // pairs per CTA: ldp / 2 threads each
+    const size_t stream = (size_t)2 * kYAsync * ppc * ldp + 2 * kYAsync * PYT, staging = (size_t)ppc * PYT * p.Px;
+    const size_t smem = (stream > staging ? stream : staging) * sizeof(float);
     cudaError_t e = cudaFuncSetAttribute(fwd_ypass_async<PYT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int grid = (npairs + ppc - 1) / ppc;
@@ -459,7 +478,8 @@ cudaError_t launch_ypass(const zl_plan_s& p, const T* t1, int ldp, const T* by, 
 cudaError_t forward_ypass_f32(const zl_plan_s& p, const float* t1, int ldp, const float* scale, float* out, int R,
                               cudaStream_t s) {
     // 16-byte rows and a kept y-basis that fits the register tile: the streaming form
-    if (ldp % 4 == 0 && p.Px <= kThreads && p.pys % 4 == 0 && (size_t)(kThreads / p.Px) * ldp * 2 * kYAsync * 4 <= 160 * 1024) {
+    if (ldp % 4 == 0 && ldp / 2 <= kThreads && p.pys % 4 == 0 &&
+        (size_t)(kThreads / (ldp / 2)) * ((size_t)ldp * 2 * kYAsync + (size_t)48 * p.Px) * 4 <= 200 * 1024) {
         const Tables<float>& t = p.tf;
         if (p.Py <= 16) return launch_ypass_async<16>(p, t1, ldp, t.byk, t.m_ipy, t.m_jx, scale, out, R, s);
         if (p.Py <= 24) return launch_ypass_async<24>(p, t1, ldp, t.byk, t.m_ipy, t.m_jx, scale, out, R, s);
