@@ -45,11 +45,15 @@ def test_status_strings(zl):
     assert "unknown" in zl.zl_status_string(99)
 
 
-@pytest.mark.parametrize("nx,ny,ell", [(64, 1, 8.0), (16, 12, 2.0), (128, 128, 10.0), (48, 48, 5.5), (7, 5, 1.3)])
+@pytest.mark.parametrize("nx,ny,ell", [(64, 1, 8.0), (16, 12, 2.0), (128, 128, 10.0), (48, 48, 5.5), (7, 5, 1.3),
+                                       (512, 512, 24.0)])
 def test_host_spectrum_matches_oracle(zl, nx, ny, ell):
+    """Per eigenvalue in relative terms, down to the smallest kept one (tau = 1e-10)."""
     lam = zl.zl_gaussian_spectrum(nx, ny, ell)
     ref = basis.spectrum_2d(nx, ny, ell)
     assert np.abs(lam - ref).max() <= 1e-13 * ref.max()
+    kept = ref > 1e-10 * ref.max()
+    assert np.max(np.abs(lam[kept] - ref[kept]) / ref[kept]) <= 1e-12
 
 
 def test_host_spectrum_rejects_bad_arguments(zl):

@@ -63,9 +63,30 @@ def test_basis_matches_rfft_packing(N):
 
 @pytest.mark.parametrize("N,ell", [(16, 1.5), (64, 8.0), (64, 5.0), (128, 10.0), (192, 28.8), (256, 16.0)])
 def test_spectrum_closed_form(N, ell):
+    """The Poisson closed form equals the definition sum_d c(d) cos(2 pi f d / N)."""
     lam = basis.spectrum_1d(N, ell)
-    cf = basis.spectrum_1d_closed_form(N, ell)
-    assert np.abs(lam - cf).max() <= 1e-12 * lam.max()
+    direct = basis.spectrum_1d_direct(N, ell)
+    assert np.abs(lam - direct).max() <= 1e-12 * lam.max()
+
+
+@pytest.mark.parametrize("N,ell", [(64, 8.0), (256, 16.0)])
+def test_spectrum_relative_accuracy_at_the_threshold(N, ell):
+    """Every eigenvalue above tau = 1e-10 (relative) to 1e-13 relative, against the definition
+    evaluated with 50 significant digits; the FP64 direct sum misses this for the smallest."""
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 50
+    P = int(np.ceil(12.0 * ell / N)) + 6
+    den = mpmath.fsum(mpmath.exp(-mpmath.mpf(p * N) ** 2 / (2 * mpmath.mpf(ell) ** 2)) for p in range(-P, P + 1))
+    c = [mpmath.fsum(mpmath.exp(-mpmath.mpf(d + p * N) ** 2 / (2 * mpmath.mpf(ell) ** 2)) for p in range(-P, P + 1)) / den
+         for d in range(N)]
+    lam = basis.spectrum_1d(N, ell)
+    f = basis.packed_frequency(N)
+    worst = 0.0
+    for i in range(N):
+        ref = mpmath.fsum(c[d] * mpmath.cos(2 * mpmath.pi * int(f[i]) * d / N) for d in range(N))
+        if ref > 1e-10 * lam.max():
+            worst = max(worst, abs(float((mpmath.mpf(lam[i]) - ref) / ref)))
+    assert worst <= 1e-13
 
 
 @pytest.mark.parametrize("N,ell", [(16, 1.5), (32, 4.0), (64, 8.0)])
