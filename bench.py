@@ -57,6 +57,22 @@ def dist_env():
     return world, rank, local
 
 
+def reduce_max(value, device):
+    """Max of a per-rank float over the default process group (identity without one)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_value(world, steps, R, seconds):
+    """Whole-job vectors/s: every rank processed steps x R right-hand sides in at most `seconds`."""
+    return world * steps * R / seconds
+
+
 # ----------------------------------------------------------------------------- bytes and peaks
 
 def element_sizes(prec):
@@ -173,18 +189,19 @@ def oracle_plan(w, prec):
     return plan, time.perf_counter() - t0
 
 
-def cpu_baseline(w, prec, nrhs=8):
-    """The oracle as it stands, on the host cores: setup untimed, then nrhs right-hand sides."""
+def cpu_baseline(w, prec, x):
+    """The oracle as it stands, on the host cores: setup untimed, then the right-hand sides x
+    (a sample of the GPU's batch).  Returns the timing record and the oracle's output."""
     from oracle import swift
     plan, t_setup = oracle_plan(w, prec)
-    x = synth.rhs(w, R=nrhs, dtype=synth.storage_dtype(prec)).astype(np.float64)
+    nrhs = len(x)
     swift.apply_left_inverse(plan, x[:1])
     t0 = time.perf_counter()
-    swift.apply_left_inverse(plan, x)
+    ref = swift.apply_left_inverse(plan, x)
     dt = time.perf_counter() - t0
     return {"value": nrhs / dt, "unit": "vectors/s", "cores": blas_threads(), "kind": "oracle",
-            "sample": f"{nrhs} right-hand sides of the full {w.name} workload through the FP64 NumPy oracle "
-                      f"(setup {t_setup:.1f} s, excluded like the GPU setup)"}
+            "sample": f"the first {nrhs} right-hand sides of the GPU batch of the full {w.name} workload through "
+                      f"the FP64 NumPy oracle (setup {t_setup:.1f} s, excluded like the GPU setup)"}, ref
 
 
 def run_reference(args, w, prec):
@@ -277,14 +294,10 @@ def run_ours(args, w, prec):
     t_wall1 = time.time()
     plan.set_stage_timing(False)
     rows = sampler.stop()
-    ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        tt = torch.tensor([ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = reduce_max(ev0.elapsed_time(ev1), dev)
     stages = plan.stage_times()
     launches = sum(n for n, _ in stages.values())
-    value = world * args.steps * R / (ms / 1e3)
+    value = aggregate_value(world, args.steps, R, ms / 1e3)
 
     # dominant kernel: the column/x-pass stage
     n_col, ms_col = stages["fwd_column"]
@@ -309,12 +322,8 @@ def run_ours(args, w, prec):
     for _ in range(args.e2e_steps):
         zl.zl_apply_left_inverse_host(plan, xh, oh, stream)
     barrier()
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        tt = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(tt.item())
-    e2e = {"value": world * args.e2e_steps * R / e2e_s, "unit": "vectors/s",
+    e2e_s = reduce_max(time.perf_counter() - t0, dev)
+    e2e = {"value": aggregate_value(world, args.e2e_steps, R, e2e_s), "unit": "vectors/s",
            "h2d_bytes_per_step": xh.numel() * xh.element_size(), "d2h_bytes_per_step": oh.numel() * oh.element_size(),
            "steps": args.e2e_steps, "api": "zl_apply_left_inverse_host (pinned host buffers)"}
 
@@ -330,7 +339,16 @@ def run_ours(args, w, prec):
         "roofline": roofline, "clocks": clocks, "e2e": e2e, "gpu_launches": launches,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(w, prec)
+        # the oracle on the first right-hand sides of this batch: a CPU timing and the GPU's accuracy
+        nchk = min(8, R)
+        xs = x[:nchk].cpu().numpy().astype(np.float64)
+        got = out[:nchk].cpu().numpy().astype(np.float64).reshape(nchk, -1)
+        line["cpu_baseline"], ref = cpu_baseline(w, prec, xs)
+        ref = ref.reshape(nchk, -1)
+        err = float(np.max(np.linalg.norm(got - ref, axis=1) / np.linalg.norm(ref, axis=1)))
+        line["accuracy"] = {"max_rel_err_vs_fp64_oracle": err, "rhs_checked": nchk,
+                            "norm": "per right-hand side ||out - ref||_2 / ||ref||_2",
+                            "tolerance": {"mixed": 1e-5, "fp32": 1e-6, "fp64": 1e-10}[prec]}
     if rank == 0:
         print(json.dumps(line), flush=True)
     plan.destroy()
