@@ -434,18 +434,28 @@ fwd_column_tc_kernel(const __grid_constant__ CUtensorMap tmap_x, const __half* _
             for (int t = rset; t < MT; t += 2) {
                 const int row = 128 * t + 32 * q + lane;
                 const int r = row >> 6, k = row & 63;
-                uint32_t dv[N2];
-                tmem_ld16(tbase + lane_off + (uint32_t)(t * N2), *reinterpret_cast<uint32_t(*)[16]>(&dv[0]));
-                tmem_ld16(tbase + lane_off + (uint32_t)(t * N2 + 16), *reinterpret_cast<uint32_t(*)[16]>(&dv[16]));
-                tmem_ld16(tbase + lane_off + (uint32_t)(t * N2 + 32), *reinterpret_cast<uint32_t(*)[16]>(&dv[32]));
+                static_assert(N2 == 48, "three 16-column TMEM loads per row");
+                uint32_t d0[16], d1[16], d2[16];
+                tmem_ld16(tbase + lane_off + (uint32_t)(t * N2), d0);
+                tmem_ld16(tbase + lane_off + (uint32_t)(t * N2 + 16), d1);
+                tmem_ld16(tbase + lane_off + (uint32_t)(t * N2 + 32), d2);
                 tmem_ld_wait();
+                tmem_regs_ready(d0);
+                tmem_regs_ready(d1);
+                tmem_regs_ready(d2);
                 if (r0 + r < R && k < K) {
                     float4* dst = reinterpret_cast<float4*>(t1 + (((size_t)y * R + r0 + r) * K + k) * pxp);
-#pragma unroll
-                    for (int c = 0; c < N2 / 4; ++c)
+                    auto put = [&](int c, const uint32_t (&d)[16], int i) {
                         if (4 * c < pxp)
-                            dst[c] = make_float4(__uint_as_float(dv[4 * c]), __uint_as_float(dv[4 * c + 1]),
-                                                 __uint_as_float(dv[4 * c + 2]), __uint_as_float(dv[4 * c + 3]));
+                            dst[c] = make_float4(__uint_as_float(d[i]), __uint_as_float(d[i + 1]), __uint_as_float(d[i + 2]),
+                                                 __uint_as_float(d[i + 3]));
+                    };
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        put(c, d0, 4 * c);
+                        put(4 + c, d1, 4 * c);
+                        put(8 + c, d2, 4 * c);
+                    }
                 }
             }
             tc_fence_before();
@@ -455,41 +465,44 @@ fwd_column_tc_kernel(const __grid_constant__ CUtensorMap tmap_x, const __half* _
 
         if (total_groups > 0 && !convert(0)) ok = false;
         if (ok && total_groups > 1 && !convert(1)) ok = false;
-        float s[GC][8];                                // w of this lane: column x rhs (8 of the unit's 16)
-        bool pending = false;                          // a finished unit whose D2 is still to be drained
-        uint32_t pending_g = 0;
-        for (uint32_t n = 0; n < 2 * total_groups && ok; ++n) {
-            const uint32_t g = n >> 1, h = n & 1u;
-            // ---- D1 of half-group n: 4 columns x (8 rhs x_hi products, 8 rhs x_lo products)
-            if (!warp_wait_bar(&bars[B_V1DONE + n % kDoneV], (n / kDoneV) & 1u, abort_flag)) { ok = false; break; }
+        // D1 of half-group n: 4 columns x (8 rhs x_hi products + 8 rhs x_lo products) -> w
+        auto drain_d1 = [&](uint32_t n, float (&w)[HG][8]) -> bool {
+            if (!warp_wait_bar(&bars[B_V1DONE + n % kDoneV], (n / kDoneV) & 1u, abort_flag)) return false;
             tc_fence_after();
-            uint32_t v[HG][16];
+            uint32_t vh[HG][8], vl[HG][8];             // products with x_hi and with x_lo
 #pragma unroll
             for (int j = 0; j < HG; ++j) {
-                tmem_ld8(tbase + lane_off + kD1Col + (uint32_t)(j * N1 + rset * 8), *reinterpret_cast<uint32_t(*)[8]>(&v[j][0]));
-                tmem_ld8(tbase + lane_off + kD1Col + (uint32_t)(j * N1 + RC + rset * 8), *reinterpret_cast<uint32_t(*)[8]>(&v[j][8]));
+                tmem_ld8(tbase + lane_off + kD1Col + (uint32_t)(j * N1 + rset * 8), vh[j]);
+                tmem_ld8(tbase + lane_off + kD1Col + (uint32_t)(j * N1 + RC + rset * 8), vl[j]);
             }
             tmem_ld_wait();
+#pragma unroll
+            for (int j = 0; j < HG; ++j) {
+                tmem_regs_ready(vh[j]);
+                tmem_regs_ready(vl[j]);
+            }
             tc_fence_before();
             mbar_arrive(&bars[B_D1EMPTY]);
-            // (two branches keep every index of s a compile-time constant: s stays in registers)
-            if (h == 0) {
 #pragma unroll
-                for (int j = 0; j < HG; ++j)
+            for (int j = 0; j < HG; ++j)
 #pragma unroll
-                    for (int rl = 0; rl < 8; ++rl) s[j][rl] = __uint_as_float(v[j][rl]) + __uint_as_float(v[j][8 + rl]);
-            } else {
-#pragma unroll
-                for (int j = 0; j < HG; ++j)
-#pragma unroll
-                    for (int rl = 0; rl < 8; ++rl) s[HG + j][rl] = __uint_as_float(v[j][rl]) + __uint_as_float(v[j][8 + rl]);
-            }
-            if (h == 0) {
-                // V1 of group g - 1 has completed, so its B operand slot takes group g + 1; the
-                // MMA thread needs that slot a whole group later, while D1 is needed right away
-                if (g >= 1 && g + 1 < total_groups && !convert(g + 1)) { ok = false; break; }
-                continue;
-            }
+                for (int rl = 0; rl < 8; ++rl) w[j][rl] = __uint_as_float(vh[j][rl]) + __uint_as_float(vl[j][rl]);
+            return true;
+        };
+
+        // One iteration per group, both V1 half-groups in sequence (the sums of the first
+        // half-group never cross a loop iteration).
+        bool pending = false;                          // a finished unit whose D2 is still to be drained
+        uint32_t pending_g = 0;
+        for (uint32_t g = 0; g < total_groups && ok; ++g) {
+            float s0[HG][8], s1[HG][8];                // w of this lane: column x rhs (8 of the unit's 16)
+            // ---- first half-group: columns 0-3
+            if (!drain_d1(2 * g, s0)) { ok = false; break; }
+            // V1 of group g - 1 has completed, so its B operand slot takes group g + 1; the MMA
+            // thread needs that slot a whole group later, while D1 is needed right away
+            if (g >= 1 && g + 1 < total_groups && !convert(g + 1)) { ok = false; break; }
+            // ---- second half-group: columns 4-7
+            if (!drain_d1(2 * g + 1, s1)) { ok = false; break; }
             // ---- the commit just seen covers the x-pass of group g - 1: W is free, and a unit that
             // ended at group g - 1 has its whole row in D2
             if (pending) {
@@ -503,15 +516,15 @@ fwd_column_tc_kernel(const __grid_constant__ CUtensorMap tmap_x, const __half* _
                 const uint32_t off = (row >> 3) * 128u + (row & 7u) * 16u;
                 if (hi_part) {
                     uint4 hi, lo;
-                    split2(s[0][rl], s[1][rl], hi.x, lo.x);
-                    split2(s[2][rl], s[3][rl], hi.y, lo.y);
-                    split2(s[4][rl], s[5][rl], hi.z, lo.z);
-                    split2(s[6][rl], s[7][rl], hi.w, lo.w);
+                    split2(s0[0][rl], s0[1][rl], hi.x, lo.x);
+                    split2(s0[2][rl], s0[3][rl], hi.y, lo.y);
+                    split2(s1[0][rl], s1[1][rl], hi.z, lo.z);
+                    split2(s1[2][rl], s1[3][rl], hi.w, lo.w);
                     *reinterpret_cast<uint4*>(sw + kWChunk + off) = hi;   // W_hi
                     *reinterpret_cast<uint4*>(sw + off) = lo;             // W_lo
                 } else {
-                    const uint4 c = make_uint4(pack_half2(s[0][rl], s[1][rl]), pack_half2(s[2][rl], s[3][rl]),
-                                               pack_half2(s[4][rl], s[5][rl]), pack_half2(s[6][rl], s[7][rl]));
+                    const uint4 c = make_uint4(pack_half2(s0[0][rl], s0[1][rl]), pack_half2(s0[2][rl], s0[3][rl]),
+                                               pack_half2(s1[0][rl], s1[1][rl]), pack_half2(s1[2][rl], s1[3][rl]));
                     *reinterpret_cast<uint4*>(sw + 2 * kWChunk + off) = c;   // W_c
                 }
             }

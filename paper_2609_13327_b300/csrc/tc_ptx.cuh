@@ -160,6 +160,16 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&v)[8]) {
 
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+// tcgen05.ld writes its destination registers asynchronously, but the compiler sees them
+// defined by the load itself and may move their uses above tcgen05.wait::ld.  Calling this
+// right after tmem_ld_wait() redefines each register in a (volatile, hence ordered) empty
+// statement after the wait, so every use depends on a point after it.
+template <int N>
+__device__ __forceinline__ void tmem_regs_ready(uint32_t (&v)[N]) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) asm volatile("" : "+r"(v[i]));
+}
+
 // Byte offset of element (row, k) of a K-major fp16 operand in the canonical
 // no-swizzle layout with the given core-matrix strides.
 __host__ __device__ __forceinline__ uint32_t kmajor_offset(uint32_t row, uint32_t k, uint32_t lbo, uint32_t sbo) {
