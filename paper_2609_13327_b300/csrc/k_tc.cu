@@ -45,8 +45,9 @@
 // L2 prefetch per group warms the images needed two groups later.
 //
 // Warp roles (352 threads): warp 0 lane 0 = producer of the pseudo-inverse
-// images and of the per-group x-pass basis, warp 1 = TMEM allocator +
-// single-thread MMA issuer, warp 2 lane 0 = producer of the x tiles, warps
+// images and of the per-group x-pass basis, warp 1 lane 0 = producer of the x
+// tiles, warp 2 = TMEM allocator + single-thread MMA issuer (warp w issues on
+// scheduler w % 4, which it shares with the two lighter W_c epilogue warps), warps
 // 3-10 = converters (x tile -> FP16 [x_hi; x_lo] B operand, two group slots)
 // and epilogue (TMEM -> W; TMEM -> intermediate t1 [ny][R][K][pxp]); two
 // epilogue warps share each TMEM lane quarter and split the unit's right-hand
@@ -89,7 +90,9 @@ constexpr int SX = 2;                  // x tile ring depth
 constexpr int SB = 3;                  // x-pass basis ring depth
 static_assert(SB == SPH, "one completion wait covers an image slot and a basis stage");
 constexpr int NEPI = 8;                // epilogue / converter warps
-constexpr int kEpiWarp0 = 3;           // warps 0: P/basis producer, 1: MMA, 2: x producer
+constexpr int kEpiWarp0 = 3;           // warps 0: P/basis producer, 1: x producer, 2: MMA
+constexpr int kMmaWarp = 2;
+constexpr int kXWarp = 1;
 constexpr int kThreadsTc = 32 * kEpiWarp0 + 32 * NEPI;
 constexpr int kEpiThreads = 32 * NEPI;
 constexpr uint32_t kD1Col = MT * N2;   // 384: V1 accumulators after the x-pass accumulators
@@ -254,7 +257,7 @@ fwd_column_tc_kernel(const __grid_constant__ CUtensorMap tmap_x, const __half* _
         fence_mbar_init();
         prefetch_tmap(&tmap_x);
     }
-    if (warp == 1) tmem_alloc(tslot, kTmemCols);
+    if (warp == kMmaWarp) tmem_alloc(tslot, kTmemCols);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -298,7 +301,7 @@ fwd_column_tc_kernel(const __grid_constant__ CUtensorMap tmap_x, const __half* _
             for (uint32_t s = 0; s < SPH; ++s) drain_slot(&bars[B_PFULL + s], pc, s, SPH);
             for (uint32_t s = 0; s < SB; ++s) drain_slot(&bars[B_BXFULL + s], bc, s, SB);
         }
-    } else if (warp == 2) {
+    } else if (warp == kXWarp) {
         // ------------------------------------------------------------ producer: x tiles
         if (lane == 0) {
             uint32_t xc = 0;
@@ -319,7 +322,7 @@ fwd_column_tc_kernel(const __grid_constant__ CUtensorMap tmap_x, const __half* _
             }
             for (uint32_t s = 0; s < SX; ++s) drain_slot(&bars[B_XFULL + s], xc, s, SX);
         }
-    } else if (warp == 1) {
+    } else if (warp == kMmaWarp) {
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
             constexpr uint32_t idesc_v1 = idesc_f16_f32(128, N1);
@@ -544,7 +547,7 @@ fwd_column_tc_kernel(const __grid_constant__ CUtensorMap tmap_x, const __half* _
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == 1) {
+    if (warp == kMmaWarp) {
         __syncwarp();
         tmem_dealloc(tbase, kTmemCols);
     }
