@@ -35,6 +35,7 @@ if ROOT not in sys.path:
 from paper_2609_13327_b300 import synth  # noqa: E402
 
 DEFAULT_WORKLOAD = "c3_256x256x32"
+BATCHED = "c4_batched"        # 200 uneven instances in one batch (synth.batched_instances)
 
 
 def parse_args():
@@ -43,7 +44,7 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(synth.WORKLOADS))
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(synth.WORKLOADS) + [BATCHED])
     ap.add_argument("--prec", default=None, choices=["fp64", "fp32", "mixed"])
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -360,8 +361,182 @@ def plan_uses_tc(plan):
     return getattr(plan, "uses_tc", lambda: False)()
 
 
+def batched_config(ws, prec):
+    return {"workload": f"{BATCHED}: {len(ws)} independent instances, square periodic grids of side 32-192, "
+                        f"4-24 levels, K 16-64, 1-32 right-hand sides each ({sum(w.R for w in ws)} per step), {prec}",
+            "instances": len(ws), "rhs_per_step": sum(w.R for w in ws), "prec": prec,
+            "l2": "no flush: one step streams every instance's x and ensemble operand (several GB) through L2"}
+
+
+def run_batched(args, prec):
+    """The batched workload: one apply of all instances per step (one CUDA graph launch)."""
+    import torch
+    world, rank, local = dist_env()
+    from paper_2609_13327_b300 import zl
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    ws = synth.batched_instances()
+    sdt = synth.storage_dtype(prec)
+    t0 = time.perf_counter()
+    # an instance whose draw has a rank-deficient column (the library reports ZL_ERR_RANK and
+    # which instance) gets a new ensemble draw; the redraws are counted in the JSON line
+    redrawn = {}
+    while True:
+        insts = [{"Z": torch.from_numpy(synth.ensemble(w, seed=w.seed + 1000003 * redrawn.get(i, 0)).astype(sdt)).to(dev),
+                  "spectrum": zl.zl_gaussian_spectrum(w.Nx, w.Ny, w.ell_loc), "nx": w.Nx, "ny": w.Ny, "prec": prec,
+                  "tau": w.tau, "max_rhs": w.R} for i, w in enumerate(ws)]
+        try:
+            batch = zl.zl_setup_batch(insts)
+            break
+        except zl.ZLError as err:
+            if err.code != zl.ZL_ERR_RANK or err.failed_instance < 0 or redrawn.get(err.failed_instance, 0) >= 3:
+                raise
+            redrawn[err.failed_instance] = redrawn.get(err.failed_instance, 0) + 1
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    del insts
+    xs = [torch.from_numpy(synth.rhs(w, seed=w.seed + 1000 * rank, dtype=sdt)).to(dev) for w in ws]
+    outs = [torch.empty((x.shape[0], p.K, p.L), dtype=x.dtype, device=dev) for x, p in zip(xs, batch.plans)]
+    stream = torch.cuda.current_stream()
+    for _ in range(max(args.warmup, 3)):
+        batch.apply_left_inverse(xs, outs, stream)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(local).uuid)
+        uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+    except Exception:
+        pass
+    sampler = ClockSampler(uuid)
+    time.sleep(0.3)
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t_wall0 = time.time()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        batch.apply_left_inverse(xs, outs, stream)
+    ev1.record(stream)
+    barrier()
+    t_wall1 = time.time()
+    rows = sampler.stop()
+    ms = reduce_max(ev0.elapsed_time(ev1), dev)
+    rhs = sum(w.R for w in ws)
+    value = aggregate_value(world, args.steps, rhs, ms / 1e3)
+    peak, peak_kind = measured_peak_hbm()
+    step_bytes = sum(algorithmic_bytes_per_rhs(w, p.L, prec, w.R) * w.R for w, p in zip(ws, batch.plans))
+    achieved = step_bytes / (ms / args.steps / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "one graph launch of all instances (per-kernel timing is not available "
+                                             "inside a graph)",
+                "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback",
+                "variants": {str(v): batch.variants.count(v) for v in sorted(set(batch.variants))},
+                "tensor_core_instances": sum(1 for p in batch.plans if p.uses_tc())}
+    # end to end: H2D of every instance's x and D2H of every x~ inside the timed loop
+    xh = [x.cpu().pin_memory() for x in xs]
+    oh = [torch.empty(o.shape, dtype=o.dtype).pin_memory() for o in outs]
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        for a, b in zip(xs, xh):
+            a.copy_(b, non_blocking=True)
+        batch.apply_left_inverse(xs, outs, stream)
+        for a, b in zip(oh, outs):
+            a.copy_(b, non_blocking=True)
+    barrier()
+    e2e_s = reduce_max(time.perf_counter() - t0, dev)
+    e2e = {"value": aggregate_value(world, args.e2e_steps, rhs, e2e_s), "unit": "vectors/s",
+           "h2d_bytes_per_step": sum(x.numel() * x.element_size() for x in xh),
+           "d2h_bytes_per_step": sum(o.numel() * o.element_size() for o in oh), "steps": args.e2e_steps,
+           "api": "zl_apply_left_inverse_batch with pinned host copies of every instance"}
+    clocks = ClockSampler.summarize(rows, t_wall0, t_wall1)
+    line = {
+        "metric": "left-inverse applications/s", "value": value, "unit": "vectors/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f16x3 split, f32 accumulate (per-instance autotuned)",
+        "data": "synthetic (seeded Gaussian-correlated ensembles, N(0,1) right-hand sides)",
+        "config": dict(batched_config(ws, prec), redrawn_rank_deficient=sorted(redrawn)), "setup_s": setup_s,
+        "roofline": roofline, "clocks": clocks, "e2e": e2e,
+        # every instance's apply is two kernels (column pass, y-pass) per pass of max_rhs right-hand sides
+        "gpu_launches": args.steps * sum(2 * ((w.R + w.R - 1) // w.R) for w in ws),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # the oracle on three instances of the batch (all their right-hand sides)
+        from oracle import basis, swift
+        errs, t_or, n_or = [], 0.0, 0
+        for i in (0, 1, 2):
+            w = ws[i]
+            Zo = synth.ensemble(w, seed=w.seed + 1000003 * redrawn.get(i, 0)).astype(sdt).astype(np.float64)
+            op = swift.Plan(Zo, w.Nx, w.Ny, basis.spectrum_2d(w.Nx, w.Ny, w.ell_loc), w.tau)
+            xo = xs[i].cpu().numpy().astype(np.float64)
+            ta = time.perf_counter()
+            ref = swift.apply_left_inverse(op, xo)
+            t_or += time.perf_counter() - ta
+            n_or += len(xo)
+            got = outs[i].cpu().numpy().astype(np.float64)
+            errs.append(float(np.max(np.linalg.norm((got - ref).reshape(len(xo), -1), axis=1) /
+                                     np.linalg.norm(ref.reshape(len(xo), -1), axis=1))))
+        line["cpu_baseline"] = {"value": n_or / t_or, "unit": "vectors/s", "cores": blas_threads(), "kind": "oracle",
+                                "sample": f"all right-hand sides of instances 0-2 of the batch ({n_or} vectors) "
+                                          f"through the FP64 NumPy oracle, setup excluded"}
+        line["accuracy"] = {"max_rel_err_vs_fp64_oracle": max(errs), "rhs_checked": n_or,
+                            "norm": "per right-hand side ||out - ref||_2 / ||ref||_2, instances 0-2",
+                            "tolerance": {"mixed": 1e-5, "fp32": 1e-6, "fp64": 1e-10}[prec]}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    batch.destroy()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def run_reference_batched(args, prec):
+    """The oracle on the batched workload: each step applies one right-hand side to each of
+    the first three instances (a bounded sample of one batch step)."""
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from oracle import basis, swift
+    ws = synth.batched_instances()[:3]
+    plans = [swift.Plan(synth.ensemble(w).astype(synth.storage_dtype(prec)).astype(np.float64), w.Nx, w.Ny,
+                        basis.spectrum_2d(w.Nx, w.Ny, w.ell_loc), w.tau) for w in ws]
+    xs = [synth.rhs(w, R=1, dtype=synth.storage_dtype(prec)).astype(np.float64) for w in ws]
+    for _ in range(args.warmup):
+        for p, x in zip(plans, xs):
+            swift.apply_left_inverse(p, x)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for p, x in zip(plans, xs):
+            swift.apply_left_inverse(p, x)
+    dt = time.perf_counter() - t0
+    value = len(ws) * args.steps / dt
+    line = {
+        "impl": "reference", "metric": "left-inverse applications/s", "value": value, "unit": "vectors/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": batched_config(synth.batched_instances(), prec),
+        "cpu_baseline": {"value": value, "unit": "vectors/s", "cores": blas_threads(), "kind": "oracle",
+                         "sample": "one right-hand side of each of instances 0-2 per step (FP64 NumPy oracle)"},
+        "e2e": {"value": value, "unit": "vectors/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
+    if args.workload == BATCHED:
+        prec = args.prec or "mixed"
+        if args.impl == "reference":
+            run_reference_batched(args, prec)
+        else:
+            run_batched(args, prec)
+        return
     w = synth.WORKLOADS[args.workload]
     prec = args.prec or w.prec
     if args.impl == "reference":

@@ -118,8 +118,9 @@ zl_status zl_get_info(zl_plan plan, int* L, int* nw, int* K, long long* nh, int*
  * whether a device-side wait has given up.  Either pointer may be NULL.
  *   tensor_core_path  1 if zl_apply_left_inverse runs the tcgen05 kernel
  *                     (ZL_MIXED plans whose shape it supports: nx a multiple of
- *                     16 and <= 256, nw <= 32, K <= 64, at most 48 kept
- *                     x-frequencies), 0 if it runs the CUDA-core kernels.
+ *                     8, nw <= 32, K <= 64, at most 48 kept x-frequencies,
+ *                     and not switched to the CUDA-core kernels by the batch
+ *                     autotuner), 0 if it runs the CUDA-core kernels.
  *   device_error      0, or the code the tensor-core kernel recorded when one
  *                     of its bounded waits timed out (the call then returns
  *                     ZL_ERR_TIMEOUT).  Reading it synchronises the device.
@@ -242,6 +243,69 @@ const char* zl_status_string(zl_status s);
  *   out  host, double[nx*ny].
  */
 zl_status zl_gaussian_spectrum(int nx, int ny, double ell, double* out);
+
+/* ------------------------------------------------------------------ batches
+ * Many independent instances (each its own grid, n_w, K, localization and
+ * number of right-hand sides) applied together.  The paper's algorithm runs
+ * on each instance unchanged (Sec. 3.9); the batch is a property of this
+ * library.
+ */
+typedef struct zl_batch_s* zl_batch;   /* opaque; owned by libzl, freed by zl_destroy_batch */
+
+/*
+ * zl_setup_batch -- one plan per instance (exactly as zl_setup would build it
+ * from descs[i], Z[i], spectra[i]; same layouts, precisions and errors), then
+ * an autotuner picks each instance's kernel variant by timing, on the
+ * instance's own shape with max_rhs right-hand sides, the variants that meet
+ * the plan's accuracy: the tcgen05 path (ZL_MIXED plans it supports) and the
+ * CUDA-core path with 8, 4, 2 or 1 right-hand sides per CTA.  Choices are
+ * cached per shape for the process and, if the environment variable
+ * ZL_AUTOTUNE_CACHE names a file, appended to and read from that file.
+ * Setup synchronises `stream` and allocates (per-plan memory plus temporary
+ * tuning buffers of the largest instance).
+ *
+ *   n                number of instances, >= 1
+ *   descs, Z, spectra  host arrays of n entries (Z[i]: device pointer)
+ *   out              receives the batch; NULL on any error (every plan built
+ *                    so far is destroyed)
+ *   failed_instance  may be NULL; receives the index of the instance whose
+ *                    setup failed, else -1
+ */
+zl_status zl_setup_batch(int n, const zl_desc* descs, const void* const* Z, const double* const* spectra,
+                         void* stream, zl_batch* out, int* failed_instance);
+
+/*
+ * zl_batch_get_info -- the plan of instance i (owned by the batch: query it
+ * with zl_get_info / zl_get_modes / zl_get_runtime_info, apply it alone with
+ * the single-plan entry points, never zl_destroy it) and the autotuned variant
+ * (0 = tcgen05 or the default heuristic, 1..4 = CUDA-core with 8, 4, 2, 1
+ * right-hand sides per CTA).  Either output may be NULL.
+ */
+zl_status zl_batch_get_info(zl_batch batch, int i, zl_plan* plan, int* variant);
+
+/*
+ * zl_apply_left_inverse_batch -- x~_i = Zh_i^- x_i for every instance i.
+ *
+ *   x, xt   host arrays of n device pointers: x[i] [R[i]][nw_i][nh_i] (read),
+ *           xt[i] [R[i]][K_i][L_i] (written); x[i] may not alias xt[i];
+ *           entries with R[i] == 0 are skipped and may be NULL
+ *   R       host array of n right-hand-side counts (>= 0; above max_rhs of an
+ *           instance its apply runs in passes)
+ *
+ * The first call with a given (x, xt, R) captures the applies of all
+ * instances into one CUDA graph (one concurrent branch per instance) and
+ * later calls with the same buffers and counts replay it with one
+ * cudaGraphLaunch on `stream`; the batch keeps the 4 most recently used
+ * graphs.  Capturing allocates nothing on the device and does not
+ * synchronise.  Calls on one batch must not overlap in host threads.
+ * Errors: ZL_ERR_ARG (null arrays, R[i] < 0, a null or aliased pair with
+ * R[i] > 0), ZL_ERR_RANK (some instance is rank-deficient), ZL_ERR_CUDA.
+ */
+zl_status zl_apply_left_inverse_batch(zl_batch batch, const void* const* x, void* const* xt, const int* R,
+                                      void* stream);
+
+/* zl_destroy_batch -- frees the batch, its plans and its graphs. */
+zl_status zl_destroy_batch(zl_batch batch);
 
 #ifdef __cplusplus
 }

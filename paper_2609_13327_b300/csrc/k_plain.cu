@@ -232,6 +232,19 @@ inv_xpass_column(const T* __restrict__ u, const T* __restrict__ M, const T* __re
     }
 }
 
+// Right-hand sides per CTA of the forward column kernel: the plan's forced choice if it
+// fits the shared-memory budget, else the largest of 8/4/2/1 that fits and has work.
+inline int pick_rc(const zl_plan_s& p, int R, size_t row) {
+    if (p.force_rc > 0 && (size_t)p.force_rc * row <= kRowSmemBudget) return p.force_rc;
+    if (R >= 8 && 8 * row <= kRowSmemBudget) return 8;
+    if (R >= 4 && 4 * row <= kRowSmemBudget) return 4;
+    if (R >= 2 && 2 * row <= kRowSmemBudget) return 2;
+    return 1;
+}
+
+template <typename T>
+cudaError_t launch_fwd(const zl_plan_s& p, const T* x, const T* M, const T* bx, T* t1, int R, cudaStream_t s);
+
 template <typename T, int RC>
 cudaError_t launch_fwd_rc(const zl_plan_s& p, const T* x, const T* M, const T* bx, T* t1, int R, cudaStream_t s) {
     const int nx = p.d.nx, ny = p.d.ny, K = p.d.K;
@@ -241,6 +254,16 @@ cudaError_t launch_fwd_rc(const zl_plan_s& p, const T* x, const T* M, const T* b
     dim3 grid((K + KC - 1) / KC, (R + RC - 1) / RC, ny);
     fwd_column_xpass<T, RC><<<grid, kThreads, smem, s>>>(x, M, bx, t1, R, p.d.nw, K, nx, ny, p.Px);
     return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_fwd(const zl_plan_s& p, const T* x, const T* M, const T* bx, T* t1, int R, cudaStream_t s) {
+    switch (pick_rc(p, R, (size_t)KC * (p.d.nx + 1) * sizeof(T))) {
+        case 8: return launch_fwd_rc<T, 8>(p, x, M, bx, t1, R, s);
+        case 4: return launch_fwd_rc<T, 4>(p, x, M, bx, t1, R, s);
+        case 2: return launch_fwd_rc<T, 2>(p, x, M, bx, t1, R, s);
+        default: return launch_fwd_rc<T, 1>(p, x, M, bx, t1, R, s);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -493,15 +516,10 @@ cudaError_t forward_ypass_f32(const zl_plan_s& p, const float* t1, int ldp, cons
 template <typename T>
 cudaError_t forward_plain(const zl_plan_s& p, const Tables<T>& t, const T* M, const T* scale, const T* x, T* out,
                           int R, cudaStream_t s) {
-    const int nx = p.d.nx;
     T* t1 = reinterpret_cast<T*>(p.t1);
     cudaError_t e;
-    const size_t row = (size_t)KC * (nx + 1) * sizeof(T);
     p.timer.begin(ZL_STAGE_FWD_COLUMN, s);
-    if (R >= 8 && 8 * row <= kRowSmemBudget) e = launch_fwd_rc<T, 8>(p, x, M, t.bx, t1, R, s);
-    else if (R >= 4 && 4 * row <= kRowSmemBudget) e = launch_fwd_rc<T, 4>(p, x, M, t.bx, t1, R, s);
-    else if (R >= 2 && 2 * row <= kRowSmemBudget) e = launch_fwd_rc<T, 2>(p, x, M, t.bx, t1, R, s);
-    else e = launch_fwd_rc<T, 1>(p, x, M, t.bx, t1, R, s);
+    e = launch_fwd<T>(p, x, M, t.bx, t1, R, s);
     p.timer.end(s);
     if (e != cudaSuccess) return e;
 
@@ -537,12 +555,7 @@ cudaError_t inverse_plain(const zl_plan_s& p, const Tables<T>& t, const T* M, co
 template <typename T>
 cudaError_t forward_plain_on(const zl_plan_s& p, const Tables<T>& t, const T* M, const T* scale, const T* x, T* out,
                              int R, cudaStream_t s, T* t1) {
-    const size_t row = (size_t)KC * (p.d.nx + 1) * sizeof(T);
-    cudaError_t e;
-    if (R >= 8 && 8 * row <= kRowSmemBudget) e = launch_fwd_rc<T, 8>(p, x, M, t.bx, t1, R, s);
-    else if (R >= 4 && 4 * row <= kRowSmemBudget) e = launch_fwd_rc<T, 4>(p, x, M, t.bx, t1, R, s);
-    else if (R >= 2 && 2 * row <= kRowSmemBudget) e = launch_fwd_rc<T, 2>(p, x, M, t.bx, t1, R, s);
-    else e = launch_fwd_rc<T, 1>(p, x, M, t.bx, t1, R, s);
+    cudaError_t e = launch_fwd<T>(p, x, M, t.bx, t1, R, s);
     if (e != cudaSuccess) return e;
     return launch_ypass<T>(p, t1, p.Px, t.by, t.m_py, t.m_jx, scale, out, R, s, &t);
 }

@@ -182,7 +182,7 @@ zl_status run(zl_plan p, Op op, const void* in, void* out, int R, void* stream) 
         } else {
             const float* x = (const float*)in + (long long)r0 * in_len;
             float* o = (float*)out + (long long)r0 * out_len;
-            if (op == Op::LeftInverse && p->d.prec == ZL_MIXED && p->tc != nullptr) {
+            if (op == Op::LeftInverse && p->d.prec == ZL_MIXED && p->tc != nullptr && !p->force_plain) {
                 e = zl::forward_tc(*p, x, o, rc, s);
             } else {
                 const float* M = (const float*)((op == Op::LeftInverse || op == Op::Adjoint) ? p->P : p->Zc);
@@ -397,7 +397,7 @@ zl_status zl_get_info(zl_plan p, int* L, int* nw, int* K, long long* nh, int* ba
 
 zl_status zl_get_runtime_info(zl_plan p, int* tensor_core_path, int* device_error) {
     if (!valid_plan(p)) return ZL_ERR_ARG;
-    if (tensor_core_path) *tensor_core_path = p->tc != nullptr ? 1 : 0;
+    if (tensor_core_path) *tensor_core_path = (p->tc != nullptr && !p->force_plain) ? 1 : 0;
     if (device_error) {
         int code = 0;
         if (zl::tc_read_error(*p, &code) != cudaSuccess) return ZL_ERR_CUDA;

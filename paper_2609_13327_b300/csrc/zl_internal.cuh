@@ -76,6 +76,12 @@ struct zl_plan_s {
     void* h_xt = nullptr;
     int* d_status = nullptr;
     mutable zl::StageTimer timer;
+    // kernel choice (set by the batch autotuner; defaults = the built-in heuristics):
+    // force_plain runs a mixed plan's left inverse on the CUDA-core FP32 kernels instead of
+    // the tensor cores, force_rc (1, 2, 4 or 8; 0 = heuristic) fixes the right-hand sides per
+    // CTA of the CUDA-core forward column kernel
+    bool force_plain = false;
+    int force_rc = 0;
 };
 
 namespace zl {

@@ -136,6 +136,25 @@ def coefficients(w, L, R=None, seed=None, dtype=np.float64):
     return rng.standard_normal((R, w.K, L), dtype=dtype)
 
 
+def batched_instances(count=200, seed=4):
+    """Uneven independent instances for the batched left inverse: square periodic grids of
+    side 32, 48, ..., 192, 4-24 levels, K in [16, 64] members (so n_w > K occurs), a
+    localization length 0.05-0.15 of the side, 1-32 right-hand sides, mixed precision.
+    The member correlation length is half the localization length, the vertical AR(1)
+    correlation 0.75, unit variances (the recipe leaves them open; these follow the other
+    workloads)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        side = int(rng.choice(np.arange(32, 193, 16)))
+        nw = int(rng.integers(4, 25))
+        K = int(rng.integers(16, 65))
+        ell_loc = float(rng.uniform(0.05, 0.15) * side)
+        R = int(rng.integers(1, 33))
+        out.append(Workload(f"c4_{i:03d}", side, side, nw, K, 0.5 * ell_loc, 0.75, ell_loc, R, "mixed", seed * 1000 + i))
+    return out
+
+
 def storage_dtype(prec):
     """Element type of every caller-visible buffer for a precision mode."""
     return np.float64 if prec == "fp64" else np.float32

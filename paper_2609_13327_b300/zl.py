@@ -28,7 +28,8 @@ PRECISIONS = {"fp64": ZL_FP64, "fp32": ZL_FP32, "mixed": ZL_MIXED}
 EXPORTS = ["zl_setup", "zl_get_info", "zl_get_modes", "zl_apply_left_inverse", "zl_apply_left_inverse_host",
            "zl_apply_sqrt", "zl_apply_adjoint", "zl_apply_sqrt_adjoint", "zl_destroy", "zl_status_string",
            "zl_gaussian_spectrum", "zl_set_stage_timing", "zl_get_stage_times", "zl_get_runtime_info",
-           "zl_apply_left_inverse_static"]
+           "zl_apply_left_inverse_static", "zl_setup_batch", "zl_batch_get_info", "zl_apply_left_inverse_batch",
+           "zl_destroy_batch"]
 STAGES = {"fwd_column": 0, "fwd_ypass": 1, "inv_ypass": 2, "inv_column": 3}
 
 
@@ -52,6 +53,11 @@ _lib.zl_gaussian_spectrum.argtypes = [_int, _int, ctypes.c_double, _dp]
 _lib.zl_set_stage_timing.argtypes = [_vp, _int]
 _lib.zl_get_runtime_info.argtypes = [_vp, _ip, _ip]
 _lib.zl_get_stage_times.argtypes = [_vp, _int, _ip, _dp]
+_lib.zl_setup_batch.argtypes = [_int, ctypes.POINTER(zl_desc), ctypes.POINTER(_vp), ctypes.POINTER(_dp), _vp,
+                                ctypes.POINTER(_vp), _ip]
+_lib.zl_batch_get_info.argtypes = [_vp, _int, ctypes.POINTER(_vp), _ip]
+_lib.zl_apply_left_inverse_batch.argtypes = [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _ip, _vp]
+_lib.zl_destroy_batch.argtypes = [_vp]
 for _name in EXPORTS:
     if _name != "zl_status_string":
         getattr(_lib, _name).restype = _int
@@ -89,9 +95,10 @@ def _stream_handle(stream):
 class Plan:
     """Owns a zl_plan handle; freed by ``destroy()`` or garbage collection."""
 
-    def __init__(self, handle, desc):
+    def __init__(self, handle, desc, owned=True):
         self.handle = handle
         self.desc = desc
+        self.owned = owned          # False for the plans of a batch (freed with the batch)
         L, nw, K, nh, bad = _int(), _int(), _int(), ctypes.c_longlong(), _int()
         _check(_lib.zl_get_info(handle, ctypes.byref(L), ctypes.byref(nw), ctypes.byref(K), ctypes.byref(nh),
                                 ctypes.byref(bad)), "zl_get_info")
@@ -136,9 +143,9 @@ class Plan:
         return out
 
     def destroy(self):
-        if self.handle:
+        if self.handle and self.owned:
             _lib.zl_destroy(self.handle)
-            self.handle = None
+        self.handle = None
 
     def __del__(self):
         try:
@@ -238,3 +245,86 @@ def zl_apply_left_inverse_host(plan, x, out=None, stream=None):
     _check(_lib.zl_apply_left_inverse_host(plan.handle, _vp(x.data_ptr()), _vp(out.data_ptr()), R,
                                            _stream_handle(stream)), "zl_apply_left_inverse_host")
     return out
+
+
+class Batch:
+    """Owns a zl_batch handle: independent instances applied together (one CUDA graph)."""
+
+    def __init__(self, handle, descs):
+        self.handle = handle
+        self.plans = []
+        self.variants = []
+        for i, d in enumerate(descs):
+            ph, v = _vp(), _int()
+            _check(_lib.zl_batch_get_info(handle, i, ctypes.byref(ph), ctypes.byref(v)), "zl_batch_get_info")
+            self.plans.append(Plan(ph, d, owned=False))
+            self.variants.append(v.value)
+
+    def __len__(self):
+        return len(self.plans)
+
+    def apply_left_inverse(self, xs, outs=None, stream=None):
+        """x~_i = Zh_i^- x_i for every instance; xs[i] [R_i][n_w][n_h] (R_i = 0 allowed)."""
+        import torch
+        n = len(self.plans)
+        if len(xs) != n:
+            raise ValueError("one input per instance")
+        if outs is None:
+            outs = [torch.empty((x.shape[0], p.K, p.L), dtype=p.dtype, device=x.device) for x, p in zip(xs, self.plans)]
+        xp, op, R = (_vp * n)(), (_vp * n)(), (_int * n)()
+        for i, (x, o, p) in enumerate(zip(xs, outs, self.plans)):
+            if not (isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == p.dtype and x.is_contiguous()
+                    and x.dim() == 3 and tuple(x.shape[1:]) == (p.nw, p.nh)):
+                raise ValueError(f"instance {i}: input must be a contiguous CUDA {p.dtype} tensor [R][{p.nw}][{p.nh}]")
+            if not (o.is_cuda and o.dtype == p.dtype and o.is_contiguous() and tuple(o.shape) == (x.shape[0], p.K, p.L)):
+                raise ValueError(f"instance {i}: bad output tensor")
+            xp[i], op[i], R[i] = x.data_ptr(), o.data_ptr(), x.shape[0]
+        _check(_lib.zl_apply_left_inverse_batch(self.handle, xp, op, R, _stream_handle(stream)),
+               "zl_apply_left_inverse_batch")
+        return outs
+
+    def destroy(self):
+        if self.handle:
+            for p in self.plans:
+                p.handle = None
+            _lib.zl_destroy_batch(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def zl_setup_batch(instances, stream=None):
+    """Build a batch from a list of instances, each a dict with keys Z (device tensor
+    [K][n_w][n_h]), spectrum (host [n_h]), nx, ny, and optionally prec, tau, max_rhs.
+    Raises ZLError; ``err.failed_instance`` names the instance whose setup failed."""
+    import torch
+    n = len(instances)
+    descs = (zl_desc * n)()
+    zs, specs, keep = (_vp * n)(), (_dp * n)(), []
+    for i, inst in enumerate(instances):
+        Z = inst["Z"]
+        p = PRECISIONS[inst.get("prec", "fp32")]
+        want = torch.float64 if p == ZL_FP64 else torch.float32
+        if not (isinstance(Z, torch.Tensor) and Z.is_cuda and Z.dtype == want and Z.dim() == 3 and Z.is_contiguous()):
+            raise ValueError(f"instance {i}: Z must be a contiguous CUDA {want} tensor [K][n_w][n_h]")
+        K, nw, nh = Z.shape
+        if inst["nx"] * inst["ny"] != nh:
+            raise ValueError(f"instance {i}: nx * ny must equal Z.shape[2]")
+        spec = np.ascontiguousarray(inst["spectrum"], dtype=np.float64)
+        if spec.shape != (nh,):
+            raise ValueError(f"instance {i}: spectrum must have n_h entries")
+        keep.append(spec)
+        descs[i] = zl_desc(inst["nx"], inst["ny"], nw, K, p, float(inst.get("tau", 1e-10)), int(inst.get("max_rhs", 32)))
+        zs[i] = Z.data_ptr()
+        specs[i] = spec.ctypes.data_as(_dp)
+    h, failed = _vp(), _int()
+    code = _lib.zl_setup_batch(n, descs, zs, specs, _stream_handle(stream), ctypes.byref(h), ctypes.byref(failed))
+    if code != ZL_OK:
+        err = ZLError(code, "zl_setup_batch")
+        err.failed_instance = failed.value
+        raise err
+    return Batch(h, [descs[i] for i in range(n)])

@@ -21,7 +21,12 @@ def main():
     per_rank_ms = 10.0 + 3.0 * rank
     ms = bench.reduce_max(per_rank_ms, torch.device("cpu"))
     value = bench.aggregate_value(world, 5, 4, ms / 1e3)
-    print(json.dumps({"rank": rank, "world": world, "ms": ms, "value": value}), flush=True)
+    mine = {"rank": rank, "world": world, "ms": ms, "value": value}
+    every = [None] * world
+    dist.all_gather_object(every, mine)        # rank 0 prints all lines: no interleaved output
+    if rank == 0:
+        sys.stdout.write("".join(json.dumps(r) + "\n" for r in every))
+        sys.stdout.flush()
     dist.barrier()
     dist.destroy_process_group()
 

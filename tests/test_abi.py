@@ -100,3 +100,17 @@ def test_applies_reject_null_plan(zl):
         assert getattr(lib, name)(None, None, None, 4, None) == zl.ZL_ERR_ARG
     assert lib.zl_get_info(None, None, None, None, None, None) == zl.ZL_ERR_ARG
     assert lib.zl_destroy(None) == zl.ZL_OK
+
+
+def test_batch_argument_errors_need_no_gpu(zl):
+    """Every batch entry point rejects bad arguments before touching the device."""
+    lib = zl._lib
+    out = ctypes.c_void_p()
+    failed = ctypes.c_int(7)
+    assert lib.zl_setup_batch(0, None, None, None, None, ctypes.byref(out), ctypes.byref(failed)) == zl.ZL_ERR_ARG
+    assert failed.value == -1 and not out.value
+    assert lib.zl_setup_batch(2, None, None, None, None, ctypes.byref(out), None) == zl.ZL_ERR_ARG
+    assert lib.zl_setup_batch(1, None, None, None, None, None, None) == zl.ZL_ERR_ARG
+    assert lib.zl_apply_left_inverse_batch(None, None, None, None, None) == zl.ZL_ERR_ARG
+    assert lib.zl_batch_get_info(None, 0, None, None) == zl.ZL_ERR_ARG
+    assert lib.zl_destroy_batch(None) == zl.ZL_ERR_ARG
