@@ -1,0 +1,46 @@
+"""Matrix-form accuracy diagnostics of a plan (the paper's Sec. 4.6-4.7 measures).
+
+* ``xi_indicators(plan)``: Xi = I - Zh^- (Zh Zh^T) Zh^-T, the deviation of the left
+  inverse from whitening the modulated-ensemble covariance P^ = Zh Zh^T (Sec. 4.6), and
+  its two indicators: the Frobenius norm (the paper's "RMSE_Xi", defined without a mean)
+  and max |Xi_ij|.  M = Zh^- Zh is formed column by column on the GPU by the library's
+  own kernels (the square root of every standardized unit vector, then the left
+  inverse), in chunks of the plan's max_rhs; Xi = I - M M^T is one plain GEMM.  Memory
+  and time grow as (K L)^2 and (K L)^3: meant for moderate sizes (K L of a few thousand).
+* ``delta(plan, xt)``: x~ - Zh^- Zh x~ per right-hand side and its 2-norm (Sec. 4.7).
+
+Every operator application runs in libzl's kernels; PyTorch supplies device memory and
+the one matrix product.
+"""
+
+import torch
+
+from . import zl
+
+
+def zh_inverse_zh(plan, stream=None):
+    """M = Zh^- Zh (K L x K L, float64 on the plan's device), built in chunks of max_rhs."""
+    KL = plan.K * plan.L
+    dev = torch.device("cuda")
+    M = torch.empty((KL, KL), dtype=torch.float64, device=dev)
+    chunk = max(1, plan.desc.max_rhs)
+    for j0 in range(0, KL, chunk):
+        n = min(chunk, KL - j0)
+        e = torch.zeros((n, plan.K, plan.L), dtype=plan.dtype, device=dev)
+        e.view(n, KL)[torch.arange(n, device=dev), j0 + torch.arange(n, device=dev)] = 1
+        cols = zl.zl_apply_left_inverse(plan, zl.zl_apply_sqrt(plan, e, stream=stream), stream=stream)
+        M[:, j0:j0 + n] = cols.view(n, KL).T.to(torch.float64)
+    return M
+
+
+def xi_indicators(plan, stream=None):
+    """(||Xi||_F, max |Xi_ij|) with Xi = I - M M^T, M = Zh^- Zh."""
+    M = zh_inverse_zh(plan, stream)
+    Xi = torch.eye(M.shape[0], dtype=torch.float64, device=M.device) - M @ M.T
+    return float(torch.linalg.matrix_norm(Xi)), float(Xi.abs().max())
+
+
+def delta(plan, xt, stream=None):
+    """x~ - Zh^- Zh x~ for x~ [R][K][L] and the 2-norm of each right-hand side."""
+    d = xt - zl.zl_apply_left_inverse(plan, zl.zl_apply_sqrt(plan, xt.contiguous(), stream=stream), stream=stream)
+    return d, torch.linalg.vector_norm(d.reshape(d.shape[0], -1).to(torch.float64), dim=1)
