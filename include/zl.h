@@ -176,6 +176,27 @@ zl_status zl_apply_adjoint(zl_plan plan, const void* y, void* g, int R, void* st
 zl_status zl_apply_sqrt_adjoint(zl_plan plan, const void* x, void* t, int R, void* stream);
 
 /*
+ * zl_standardize_ensemble -- a forecast ensemble in standardized variables
+ * (Sec. 2.1-2.2): row j of the output is Zh^- (e_j - mean) / sqrt(K_f - 1), the
+ * standardized variables transform applied to forecast perturbation j, so that
+ * P~^e = sum_j xt_j xt_j^T is the standardized ensemble covariance that the
+ * Hybrid suggested in Sec. 2.2 localizes.
+ *
+ *   members  device, [K_f][nw][ny*nx]: the forecast members e_j (not centred),
+ *            read only
+ *   xt       device, [K_f][K][L], written; may not alias members
+ *   Kf       number of forecast members, >= 2 (above max_rhs the left inverse
+ *            runs in passes)
+ *
+ * Zh^- is linear: the members are mapped by the plan's left-inverse kernels and
+ * the centring over members and the 1/sqrt(K_f - 1) scaling are applied to the
+ * coefficients (mean accumulated in FP64).  Allocates nothing.
+ * Errors: ZL_ERR_ARG (null pointers, aliasing, K_f < 2), and those of
+ * zl_apply_left_inverse.
+ */
+zl_status zl_standardize_ensemble(zl_plan plan, const void* members, void* xt, int Kf, void* stream);
+
+/*
  * Stage timing (profiling aid).  Each apply runs two kernel stages:
  *   ZL_STAGE_FWD_COLUMN  per-column product fused with the x-pass of V_b^T
  *                        (left inverse and Zh^T; the dominant kernel)

@@ -29,7 +29,7 @@ EXPORTS = ["zl_setup", "zl_get_info", "zl_get_modes", "zl_apply_left_inverse", "
            "zl_apply_sqrt", "zl_apply_adjoint", "zl_apply_sqrt_adjoint", "zl_destroy", "zl_status_string",
            "zl_gaussian_spectrum", "zl_set_stage_timing", "zl_get_stage_times", "zl_get_runtime_info",
            "zl_apply_left_inverse_static", "zl_setup_batch", "zl_batch_get_info", "zl_apply_left_inverse_batch",
-           "zl_destroy_batch"]
+           "zl_destroy_batch", "zl_standardize_ensemble"]
 STAGES = {"fwd_column": 0, "fwd_ypass": 1, "inv_ypass": 2, "inv_column": 3}
 
 
@@ -44,7 +44,7 @@ _lib.zl_setup.argtypes = [ctypes.POINTER(zl_desc), _vp, _dp, _vp, ctypes.POINTER
 _lib.zl_get_info.argtypes = [_vp, _ip, _ip, _ip, _llp, _ip]
 _lib.zl_get_modes.argtypes = [_vp, _ip]
 for _name in ("zl_apply_left_inverse", "zl_apply_left_inverse_host", "zl_apply_sqrt", "zl_apply_adjoint",
-              "zl_apply_sqrt_adjoint", "zl_apply_left_inverse_static"):
+              "zl_apply_sqrt_adjoint", "zl_apply_left_inverse_static", "zl_standardize_ensemble"):
     getattr(_lib, _name).argtypes = [_vp, _vp, _vp, _int, _vp]
 _lib.zl_destroy.argtypes = [_vp]
 _lib.zl_status_string.argtypes = [_int]
@@ -207,6 +207,14 @@ def zl_apply_left_inverse(plan, x, out=None, stream=None):
     """x~ = Zh^- x: x [R][n_w][n_h] -> x~ [R][K][L]."""
     return _apply(_lib.zl_apply_left_inverse, plan, x, (plan.nw, plan.nh), (plan.K, plan.L), out, stream,
                   "zl_apply_left_inverse")
+
+
+def zl_standardize_ensemble(plan, members, out=None, stream=None):
+    """Forecast members e [K_f][n_w][n_h] -> Zh^- (e_j - mean) / sqrt(K_f - 1), [K_f][K][L]."""
+    if members.dim() == 3 and members.shape[0] < 2:
+        raise ValueError("zl_standardize_ensemble: at least two members")
+    return _apply(_lib.zl_standardize_ensemble, plan, members, (plan.nw, plan.nh), (plan.K, plan.L), out, stream,
+                  "zl_standardize_ensemble")
 
 
 def zl_apply_left_inverse_static(plan, x, out=None, stream=None):

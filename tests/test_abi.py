@@ -114,3 +114,7 @@ def test_batch_argument_errors_need_no_gpu(zl):
     assert lib.zl_apply_left_inverse_batch(None, None, None, None, None) == zl.ZL_ERR_ARG
     assert lib.zl_batch_get_info(None, 0, None, None) == zl.ZL_ERR_ARG
     assert lib.zl_destroy_batch(None) == zl.ZL_ERR_ARG
+
+
+def test_standardize_ensemble_rejects_null_plan(zl):
+    assert zl._lib.zl_standardize_ensemble(None, None, None, 4, None) == zl.ZL_ERR_ARG
