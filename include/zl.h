@@ -128,6 +128,20 @@ zl_status zl_get_info(zl_plan plan, int* L, int* nw, int* K, long long* nh, int*
 zl_status zl_get_runtime_info(zl_plan plan, int* tensor_core_path, int* device_error);
 
 /*
+ * zl_set_test_wait_timeout -- a test hook of the failure-detection path; the
+ * paper has no counterpart.  enable = 1: from the next apply on, the
+ * tensor-core kernel's image producer issues no copies, so the MMA thread's
+ * bounded wait for the first image runs out (about 2 s), the kernel records a
+ * nonzero device error, frees its TMEM and returns; the results of such an
+ * apply are undefined and zl_get_runtime_info reports ZL_ERR_TIMEOUT.
+ * enable = 0: restores normal operation and clears the recorded device error.
+ * No GPU fault is involved and the context stays usable.  The call
+ * synchronises the device.  Errors: ZL_ERR_ARG (invalid plan, enable not 0 or
+ * 1), ZL_ERR_UNSUPPORTED (the plan has no tensor-core path), ZL_ERR_CUDA.
+ */
+zl_status zl_set_test_wait_timeout(zl_plan plan, int enable);
+
+/*
  * zl_get_modes -- the kept packed mode indices s (ascending), host int[L].
  * Output coefficient j of every member refers to mode modes[j].
  */

@@ -211,7 +211,7 @@ template <int NWP>
 __global__ void __launch_bounds__(kThreadsTc, 1)
 fwd_column_tc_kernel(const __grid_constant__ CUtensorMap tmap_x, const __half* __restrict__ pimg,
                      const uint8_t* __restrict__ bximg, float* __restrict__ t1, int* __restrict__ err,
-                     int R, int K, int nx, int ny, int pxp) {
+                     int R, int K, int nx, int ny, int pxp, int starve) {
     constexpr int nwp = NWP;
     extern __shared__ __align__(1024) uint8_t smem[];
     constexpr SmemPlan sp = smem_plan(NWP);
@@ -265,7 +265,9 @@ fwd_column_tc_kernel(const __grid_constant__ CUtensorMap tmap_x, const __half* _
 
     if (warp == 0) {
         // ------------------------------------------------------------ producer: images + x-pass basis
-        if (lane == 0) {
+        // (starve: a test of the failure path; no copy is issued, so the MMA thread's bounded
+        // wait for the first image runs out)
+        if (lane == 0 && !starve) {
             uint32_t pc = 0, bc = 0;           // half-groups, basis stages issued
             for (uint32_t n = 0; n < 2 * total_groups; ++n) {
                 const uint32_t gi = n >> 1;
@@ -684,6 +686,11 @@ void tc_release(zl_plan_s& p) {
 
 int tc_t1_stride(const zl_plan_s& p) { return p.tc ? p.tc->pxp : p.Px; }
 
+cudaError_t tc_clear_error(const zl_plan_s& p) {
+    if (!p.tc) return cudaSuccess;
+    return cudaMemset(p.tc->d_err, 0, sizeof(int));
+}
+
 cudaError_t tc_read_error(const zl_plan_s& p, int* code) {
     *code = 0;
     if (!p.tc) return cudaSuccess;
@@ -706,10 +713,12 @@ cudaError_t forward_tc(const zl_plan_s& p, const float* x, float* out, int R, cu
     p.timer.begin(ZL_STAGE_FWD_COLUMN, s);
     if (t.nwp == 16)
         fwd_column_tc_kernel<16><<<grid, kThreadsTc, t.smem, s>>>(tmap, t.pimg, t.bximg, reinterpret_cast<float*>(p.t1),
-                                                                  t.d_err, R, p.d.K, p.d.nx, p.d.ny, t.pxp);
+                                                                  t.d_err, R, p.d.K, p.d.nx, p.d.ny, t.pxp,
+                                                                  p.test_wait_timeout);
     else
         fwd_column_tc_kernel<32><<<grid, kThreadsTc, t.smem, s>>>(tmap, t.pimg, t.bximg, reinterpret_cast<float*>(p.t1),
-                                                                  t.d_err, R, p.d.K, p.d.nx, p.d.ny, t.pxp);
+                                                                  t.d_err, R, p.d.K, p.d.nx, p.d.ny, t.pxp,
+                                                                  p.test_wait_timeout);
     p.timer.end(s);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

@@ -407,6 +407,15 @@ zl_status zl_get_runtime_info(zl_plan p, int* tensor_core_path, int* device_erro
     return ZL_OK;
 }
 
+zl_status zl_set_test_wait_timeout(zl_plan p, int enable) {
+    if (!valid_plan(p) || (enable != 0 && enable != 1)) return ZL_ERR_ARG;
+    if (p->tc == nullptr) return ZL_ERR_UNSUPPORTED;
+    if (cudaDeviceSynchronize() != cudaSuccess) return ZL_ERR_CUDA;
+    p->test_wait_timeout = enable;
+    if (!enable && zl::tc_clear_error(*p) != cudaSuccess) return ZL_ERR_CUDA;
+    return ZL_OK;
+}
+
 zl_status zl_get_modes(zl_plan p, int* modes) {
     if (!valid_plan(p) || modes == nullptr) return ZL_ERR_ARG;
     std::copy(p->modes.begin(), p->modes.end(), modes);

@@ -82,6 +82,9 @@ struct zl_plan_s {
     // CTA of the CUDA-core forward column kernel
     bool force_plain = false;
     int force_rc = 0;
+    // test hook of the failure-detection path (zl_set_test_wait_timeout): the tensor-core
+    // kernel's image producer issues no copies, so a bounded wait runs out
+    int test_wait_timeout = 0;
 };
 
 namespace zl {
@@ -114,5 +117,6 @@ zl_status tc_prepare(zl_plan_s& p, cudaStream_t s);
 void tc_release(zl_plan_s& p);
 cudaError_t forward_tc(const zl_plan_s& p, const float* x, float* out, int R, cudaStream_t s);
 cudaError_t tc_read_error(const zl_plan_s& p, int* code);
+cudaError_t tc_clear_error(const zl_plan_s& p);
 
 }  // namespace zl

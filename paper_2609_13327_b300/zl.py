@@ -29,7 +29,7 @@ EXPORTS = ["zl_setup", "zl_get_info", "zl_get_modes", "zl_apply_left_inverse", "
            "zl_apply_sqrt", "zl_apply_adjoint", "zl_apply_sqrt_adjoint", "zl_destroy", "zl_status_string",
            "zl_gaussian_spectrum", "zl_set_stage_timing", "zl_get_stage_times", "zl_get_runtime_info",
            "zl_apply_left_inverse_static", "zl_setup_batch", "zl_batch_get_info", "zl_apply_left_inverse_batch",
-           "zl_destroy_batch", "zl_standardize_ensemble"]
+           "zl_destroy_batch", "zl_standardize_ensemble", "zl_set_test_wait_timeout"]
 STAGES = {"fwd_column": 0, "fwd_ypass": 1, "inv_ypass": 2, "inv_column": 3}
 
 
@@ -52,6 +52,7 @@ _lib.zl_status_string.restype = ctypes.c_char_p
 _lib.zl_gaussian_spectrum.argtypes = [_int, _int, ctypes.c_double, _dp]
 _lib.zl_set_stage_timing.argtypes = [_vp, _int]
 _lib.zl_get_runtime_info.argtypes = [_vp, _ip, _ip]
+_lib.zl_set_test_wait_timeout.argtypes = [_vp, _int]
 _lib.zl_get_stage_times.argtypes = [_vp, _int, _ip, _dp]
 _lib.zl_setup_batch.argtypes = [_int, ctypes.POINTER(zl_desc), ctypes.POINTER(_vp), ctypes.POINTER(_dp), _vp,
                                 ctypes.POINTER(_vp), _ip]
@@ -129,6 +130,11 @@ class Plan:
         if rc not in (ZL_OK, ZL_ERR_TIMEOUT):
             _check(rc, "zl_get_runtime_info")
         return code.value
+
+    def set_test_wait_timeout(self, enable):
+        """Test hook: the tensor-core kernel's bounded wait runs out (enable) / normal
+        operation with the device error cleared (disable).  Synchronises the device."""
+        _check(_lib.zl_set_test_wait_timeout(self.handle, 1 if enable else 0), "zl_set_test_wait_timeout")
 
     def set_stage_timing(self, enable):
         _check(_lib.zl_set_stage_timing(self.handle, 1 if enable else 0), "zl_set_stage_timing")

@@ -118,3 +118,9 @@ def test_batch_argument_errors_need_no_gpu(zl):
 
 def test_standardize_ensemble_rejects_null_plan(zl):
     assert zl._lib.zl_standardize_ensemble(None, None, None, 4, None) == zl.ZL_ERR_ARG
+
+
+def test_wait_timeout_hook_rejects_bad_arguments(zl):
+    lib = zl._lib
+    assert lib.zl_set_test_wait_timeout(None, 1) == zl.ZL_ERR_ARG
+    assert lib.zl_set_test_wait_timeout(None, 0) == zl.ZL_ERR_ARG
