@@ -340,10 +340,13 @@ fwd_ypass_gemm(const T* __restrict__ t1, const T* __restrict__ byk, const int* _
 // FP32 y-pass with the t1 rows of the CTA's pairs and the kept y-basis rows streamed
 // through double-buffered shared memory by cp.async (16-byte copies), so that enough
 // bytes are in flight to run at memory speed.  Needs ldp % 4 == 0 (16-byte rows).
-// Each thread accumulates two adjacent x-frequencies of one (rhs, member) pair for all
-// kept y-frequencies: one 8-byte load of t1 and PYT/4 broadcast 16-byte loads of the
-// y-basis feed 2 PYT FMAs, so the loop is bound by the FMA pipes rather than by the
-// shared-memory load pipe.  The output staging reuses the stream's shared memory.
+// Each thread accumulates two adjacent x-frequencies (a column pair) of one (rhs,
+// member) pair with packed two-lane FMAs (fma.rn.f32x2: two round-to-nearest FP32
+// FMAs, the same arithmetic as two fmaf).  Threads are numbered column-major (the
+// pairs of the CTA vary fastest), so a warp spans two or three neighbouring column
+// pairs; each thread needs only the kept y-rows 0 .. yneed(jx) - 1 of its columns, and
+// the warp runs the largest of its lanes' row counts, chosen once per streamed chunk.
+// The output staging reuses the stream's shared memory.
 constexpr int kYAsync = 16;
 
 __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
@@ -354,22 +357,79 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
+__device__ __forceinline__ uint64_t f32x2_splat(float v) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %1};" : "=l"(r) : "f"(v));
+    return r;
+}
+__device__ __forceinline__ void f32x2_fma(uint64_t& acc, uint64_t a, uint64_t b) {
+    asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc) : "l"(a), "l"(b));
+}
+__device__ __forceinline__ float2 f32x2_unpack(uint64_t v) {
+    float2 r;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+    return r;
+}
+
+// yn streamed y-rows of one column pair: kept y-rows 0 .. 4 N4 - 1 (a0: column jx, a1: jx + 1;
+// entry i holds y-rows 2i and 2i + 1).
+template <int PYT, int N4>
+__device__ __forceinline__ void ypass_rows(uint64_t (&a0)[PYT / 2], uint64_t (&a1)[PYT / 2], const float* tt,
+                                           const float* bb, int yn, int pw) {
+#pragma unroll 1
+    for (int yy = 0; yy < yn; ++yy) {
+        const float2 tv = *reinterpret_cast<const float2*>(tt + yy * pw);
+        const uint64_t tx = f32x2_splat(tv.x), ty = f32x2_splat(tv.y);
+        const ulonglong2* b = reinterpret_cast<const ulonglong2*>(bb + yy * PYT);
+#pragma unroll
+        for (int i = 0; i < N4; ++i) {
+            const ulonglong2 bv = b[i];
+            f32x2_fma(a0[2 * i], bv.x, tx);
+            f32x2_fma(a0[2 * i + 1], bv.y, tx);
+            f32x2_fma(a1[2 * i], bv.x, ty);
+            f32x2_fma(a1[2 * i + 1], bv.y, ty);
+        }
+    }
+}
+
+// ypass_rows<PYT, n4> for a warp-uniform n4 in 1 .. N4
+template <int PYT, int N4>
+__device__ __forceinline__ void ypass_rows_n(int n4, uint64_t (&a0)[PYT / 2], uint64_t (&a1)[PYT / 2],
+                                             const float* tt, const float* bb, int yn, int pw) {
+    if constexpr (N4 >= 1) {
+        if (n4 == N4)
+            ypass_rows<PYT, N4>(a0, a1, tt, bb, yn, pw);
+        else
+            ypass_rows_n<PYT, N4 - 1>(n4, a0, a1, tt, bb, yn, pw);
+    }
+}
+
 template <int PYT>
 __global__ void __launch_bounds__(kThreads)
 fwd_ypass_async(const float* __restrict__ t1, const float* __restrict__ byk, const int* __restrict__ m_ipy,
-                const int* __restrict__ m_jx, const float* __restrict__ scale, float* __restrict__ out,
-                int npairs, int ppc, int ny, int Px, int ldp, int L, int pys) {
+                const int* __restrict__ m_jx, const int* __restrict__ yneed, const float* __restrict__ scale,
+                float* __restrict__ out, int npairs, int ppc, int ny, int Px, int ldp, int L, int pys) {
+    static_assert(PYT % 8 == 0, "16-byte rows of the kept y-basis");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int pw = ppc * ldp;                                   // floats of one y-row of this CTA
     float* st = reinterpret_cast<float*>(smem_raw);             // [2][kYAsync][pw]
     float* sb = st + 2 * kYAsync * pw;                          // [2][kYAsync][PYT]
-    float* sout = st;                                           // [ppc][PYT][Px], after the stream
+    float* sout = st;                                           // [ppc][spitch], after the stream
+    const int spitch = PYT * Px + 1;                            // odd: the lanes' stores hit distinct banks
     const int tid = threadIdx.x;
-    const int half = ldp / 2;                                   // threads per pair
-    const int pl = tid / half, jx = 2 * (tid - pl * half);      // columns jx, jx + 1
+    const int half = ldp / 2;                                   // column pairs
+    const int cp = tid / ppc, pl = tid - cp * ppc;              // column pair, pair in the CTA
+    const int jx = 2 * cp;                                      // columns jx, jx + 1
     const long long pair0 = (long long)blockIdx.x * ppc;
     const int npl = (int)min((long long)ppc, npairs - pair0);  // pairs this CTA really has
-    const bool active = pl < npl;
+    const bool active = cp < half && pl < npl;
+    int need = 0;
+    if (active) {
+        if (jx < Px) need = yneed[jx];
+        if (jx + 1 < Px) need = max(need, yneed[jx + 1]);
+    }
+    const int n4 = (need + 3) >> 2;                             // 16-byte groups of kept y-rows
+    const int n4w = __reduce_max_sync(0xffffffffu, n4);         // the warp's row groups
     const long long ystride = (long long)npairs * ldp;
     const int nchunk = (ny + kYAsync - 1) / kYAsync;
     auto issue = [&](int c) {
@@ -388,9 +448,9 @@ fwd_ypass_async(const float* __restrict__ t1, const float* __restrict__ byk, con
         }
         cp_async_commit();
     };
-    float acc0[PYT], acc1[PYT];
+    uint64_t a0[PYT / 2], a1[PYT / 2];
 #pragma unroll
-    for (int i = 0; i < PYT; ++i) acc0[i] = acc1[i] = 0.f;
+    for (int i = 0; i < PYT / 2; ++i) a0[i] = a1[i] = 0ull;
     issue(0);
     for (int c = 0; c < nchunk; ++c) {
         if (c + 1 < nchunk) {
@@ -403,37 +463,29 @@ fwd_ypass_async(const float* __restrict__ t1, const float* __restrict__ byk, con
         const int yn = min(kYAsync, ny - c * kYAsync);
         const float* tt = st + (c & 1) * kYAsync * pw + pl * ldp + jx;
         const float* bb = sb + (c & 1) * kYAsync * PYT;
-        if (active) {
-            for (int yy = 0; yy < yn; ++yy) {
-                const float2 tv = *reinterpret_cast<const float2*>(tt + yy * pw);
-                const float4* b = reinterpret_cast<const float4*>(bb + yy * PYT);
-#pragma unroll
-                for (int i = 0; i < PYT / 4; ++i) {
-                    const float4 bv = b[i];
-                    acc0[4 * i] = fmaf(bv.x, tv.x, acc0[4 * i]);
-                    acc1[4 * i] = fmaf(bv.x, tv.y, acc1[4 * i]);
-                    acc0[4 * i + 1] = fmaf(bv.y, tv.x, acc0[4 * i + 1]);
-                    acc1[4 * i + 1] = fmaf(bv.y, tv.y, acc1[4 * i + 1]);
-                    acc0[4 * i + 2] = fmaf(bv.z, tv.x, acc0[4 * i + 2]);
-                    acc1[4 * i + 2] = fmaf(bv.z, tv.y, acc1[4 * i + 2]);
-                    acc0[4 * i + 3] = fmaf(bv.w, tv.x, acc0[4 * i + 3]);
-                    acc1[4 * i + 3] = fmaf(bv.w, tv.y, acc1[4 * i + 3]);
-                }
-            }
-        }
+        if (active) ypass_rows_n<PYT, PYT / 4>(n4w, a0, a1, tt, bb, yn, pw);
         __syncthreads();   // the buffer of chunk c is refilled by issue(c + 2)
     }
     if (active) {
-        float* so = sout + (size_t)pl * PYT * Px;
+        float* so = sout + (size_t)pl * spitch;
 #pragma unroll
-        for (int i = 0; i < PYT; ++i) {
-            if (jx < Px) so[i * Px + jx] = acc0[i];
-            if (jx + 1 < Px) so[i * Px + jx + 1] = acc1[i];
+        for (int i = 0; i < PYT / 2; ++i) {
+            if (2 * i < 4 * n4) {                              // rows past yneed are never gathered
+                const float2 c0 = f32x2_unpack(a0[i]), c1 = f32x2_unpack(a1[i]);
+                if (jx < Px) {
+                    so[(2 * i) * Px + jx] = c0.x;
+                    so[(2 * i + 1) * Px + jx] = c0.y;
+                }
+                if (jx + 1 < Px) {
+                    so[(2 * i) * Px + jx + 1] = c1.x;
+                    so[(2 * i + 1) * Px + jx + 1] = c1.y;
+                }
+            }
         }
     }
     __syncthreads();
     for (int pp = 0; pp < npl; ++pp) {
-        const float* so = sout + (size_t)pp * PYT * Px;
+        const float* so = sout + (size_t)pp * spitch;
         float* o = out + (pair0 + pp) * L;
         for (int j = tid; j < L; j += blockDim.x) o[j] = so[m_ipy[j] * Px + m_jx[j]] * scale[j];
     }
@@ -441,17 +493,19 @@ fwd_ypass_async(const float* __restrict__ t1, const float* __restrict__ byk, con
 
 template <int PYT>
 cudaError_t launch_ypass_async(const zl_plan_s& p, const float* t1, int ldp, const float* byk, const int* m_ipy,
-                               const int* m_jx, const float* scale, float* out, int R, cudaStream_t s) {
+                               const int* m_jx, const int* yneed, const float* scale, float* out, int R,
+                               cudaStream_t s) {
     const int npairs = R * p.d.K;
     const int ppc = kThreads / (ldp / 2);                       // pairs per CTA: ldp / 2 threads each
-    const size_t stream = (size_t)2 * kYAsync * ppc * ldp + 2 * kYAsync * PYT, staging = (size_t)ppc * PYT * p.Px;
+    const size_t stream = (size_t)2 * kYAsync * ppc * ldp + 2 * kYAsync * PYT,
+                 staging = (size_t)ppc * ((size_t)PYT * p.Px + 1);
     const size_t smem = (stream > staging ? stream : staging) * sizeof(float);
     cudaError_t e = cudaFuncSetAttribute(fwd_ypass_async<PYT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int grid = (npairs + ppc - 1) / ppc;
     p.timer.begin(ZL_STAGE_FWD_YPASS, s);
-    fwd_ypass_async<PYT><<<grid, kThreads, smem, s>>>(t1, byk, m_ipy, m_jx, scale, out, npairs, ppc, p.d.ny, p.Px, ldp,
-                                                      p.L, p.pys);
+    fwd_ypass_async<PYT><<<grid, kThreads, smem, s>>>(t1, byk, m_ipy, m_jx, yneed, scale, out, npairs, ppc, p.d.ny,
+                                                      p.Px, ldp, p.L, p.pys);
     p.timer.end(s);
     return cudaGetLastError();
 }
@@ -504,11 +558,11 @@ cudaError_t forward_ypass_f32(const zl_plan_s& p, const float* t1, int ldp, cons
     if (ldp % 4 == 0 && ldp / 2 <= kThreads && p.pys % 4 == 0 &&
         (size_t)(kThreads / (ldp / 2)) * ((size_t)ldp * 2 * kYAsync + (size_t)48 * p.Px) * 4 <= 200 * 1024) {
         const Tables<float>& t = p.tf;
-        if (p.Py <= 16) return launch_ypass_async<16>(p, t1, ldp, t.byk, t.m_ipy, t.m_jx, scale, out, R, s);
-        if (p.Py <= 24) return launch_ypass_async<24>(p, t1, ldp, t.byk, t.m_ipy, t.m_jx, scale, out, R, s);
-        if (p.Py <= 32) return launch_ypass_async<32>(p, t1, ldp, t.byk, t.m_ipy, t.m_jx, scale, out, R, s);
-        if (p.Py <= 40) return launch_ypass_async<40>(p, t1, ldp, t.byk, t.m_ipy, t.m_jx, scale, out, R, s);
-        if (p.Py <= 48) return launch_ypass_async<48>(p, t1, ldp, t.byk, t.m_ipy, t.m_jx, scale, out, R, s);
+        if (p.Py <= 16) return launch_ypass_async<16>(p, t1, ldp, t.byk, t.m_ipy, t.m_jx, t.yneed, scale, out, R, s);
+        if (p.Py <= 24) return launch_ypass_async<24>(p, t1, ldp, t.byk, t.m_ipy, t.m_jx, t.yneed, scale, out, R, s);
+        if (p.Py <= 32) return launch_ypass_async<32>(p, t1, ldp, t.byk, t.m_ipy, t.m_jx, t.yneed, scale, out, R, s);
+        if (p.Py <= 40) return launch_ypass_async<40>(p, t1, ldp, t.byk, t.m_ipy, t.m_jx, t.yneed, scale, out, R, s);
+        if (p.Py <= 48) return launch_ypass_async<48>(p, t1, ldp, t.byk, t.m_ipy, t.m_jx, t.yneed, scale, out, R, s);
     }
     return launch_ypass<float>(p, t1, ldp, p.tf.by, p.tf.m_py, p.tf.m_jx, scale, out, R, s, &p.tf);
 }

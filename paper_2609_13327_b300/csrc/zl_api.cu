@@ -95,8 +95,11 @@ cudaError_t build_tables(zl_plan_s& p, zl::Tables<T>& t, const std::vector<doubl
             yslot[q] = (int)pylist.size();
             pylist.push_back(q);
         }
-    std::vector<int> ipy(L);
-    for (int j = 0; j < L; ++j) ipy[j] = yslot[py[j]];
+    std::vector<int> ipy(L), yneed(Px, 0);
+    for (int j = 0; j < L; ++j) {
+        ipy[j] = yslot[py[j]];
+        yneed[jxv[j]] = std::max(yneed[jxv[j]], ipy[j] + 1);
+    }
     std::vector<T> byk((size_t)ny * p.pys, (T)0);
     for (int y = 0; y < ny; ++y)
         for (size_t i = 0; i < pylist.size(); ++i) byk[(size_t)y * p.pys + i] = (T)basis_value(ny, pylist[i], y);
@@ -115,6 +118,7 @@ cudaError_t build_tables(zl_plan_s& p, zl::Tables<T>& t, const std::vector<doubl
     if ((e = upload(&t.grp_start, gstart, s)) != cudaSuccess) return e;
     if ((e = upload(&t.m_ipy, ipy, s)) != cudaSuccess) return e;
     if ((e = upload(&t.byk, byk, s)) != cudaSuccess) return e;
+    if ((e = upload(&t.yneed, yneed, s)) != cudaSuccess) return e;
     return upload(&t.grp_modes, gmodes, s);
 }
 
@@ -130,6 +134,7 @@ void free_tables(zl::Tables<T>& t) {
     cudaFree(t.grp_modes);
     cudaFree(t.m_ipy);
     cudaFree(t.byk);
+    cudaFree(t.yneed);
     t = zl::Tables<T>();
 }
 

@@ -28,6 +28,7 @@ struct Tables {
     int* grp_modes = nullptr;
     int* m_ipy = nullptr;   // [L] index of mode j's p_y in the list of kept y-frequencies
     T* byk = nullptr;       // [ny][pys] b_{p_y}(y) of the kept y-frequencies, zero-padded to pys
+    int* yneed = nullptr;   // [Px] 1 + the largest m_ipy among the kept modes of x-frequency jx
 };
 
 struct TcOperands;   // tensor-core path state (k_tc.cu)

@@ -5,7 +5,8 @@ Checks that the tensor-core kernel is really the one that runs
 matches the oracle within the mixed-precision tolerance 1e-5 (relative 2-norm
 per right-hand side) on shapes that exercise every padded path: ragged numbers
 of right-hand sides (partial 16-rhs units), fewer than 64 members, fewer than
-16 levels, and several rows per CTA.
+16 levels, several rows per CTA, and every row tier (16 to 48 kept
+y-frequencies) of the y-pass.
 """
 
 import numpy as np
@@ -39,6 +40,10 @@ CASES = [
     synth.Workload("tc_small_K", 32, 12, 10, 40, 4.0, 0.7, 3.0, 21, "mixed", 32),
     synth.Workload("tc_16_levels", 64, 24, 16, 48, 6.0, 0.75, 5.0, 35, "mixed", 33),
     synth.Workload("tc_one_row_many_rhs", 128, 2, 24, 64, 6.0, 0.7, 8.0, 64, "mixed", 34),
+    # 47, 31 and 17 kept y-frequencies: the 48-, 32- and 24-row tiers of the y-pass
+    synth.Workload("tc_py47", 64, 64, 16, 48, 6.0, 0.7, 3.0, 19, "mixed", 36),
+    synth.Workload("tc_py31", 64, 64, 24, 40, 6.0, 0.75, 4.5, 23, "mixed", 37),
+    synth.Workload("tc_py17", 64, 48, 8, 32, 4.0, 0.7, 6.0, 11, "mixed", 38),
 ]
 
 
