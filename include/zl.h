@@ -161,9 +161,16 @@ zl_status zl_apply_left_inverse(zl_plan plan, const void* x, void* xt, int R, vo
 /*
  * zl_apply_left_inverse_host -- the same operator on HOST buffers: copies x to
  * the device, applies, copies x~ back, and synchronises `stream`.  x and xt
- * should be page-locked for the copies to be asynchronous.  The device staging
- * buffers are owned by the plan and allocated on first use (this is the only
- * entry point that may allocate after setup).
+ * should be page-locked for the copies to be asynchronous.  The right-hand
+ * sides go in pieces (about max_rhs / 4, at least 16): the copy-in of a piece
+ * runs on an internal stream while the kernels of the previous piece run on
+ * `stream` and the copy-back of the one before runs on a second internal
+ * stream.  The copies start after the work already queued on `stream`.  When
+ * the call returns, on success or error, nothing it queued is still running.
+ * The device staging (two pieces of x and of x~), the two streams and the
+ * events are owned by the plan and created on first use (this is the only
+ * entry point that may allocate after setup).  Not safe to call concurrently
+ * on one plan.
  */
 zl_status zl_apply_left_inverse_host(zl_plan plan, const void* x, void* xt, int R, void* stream);
 

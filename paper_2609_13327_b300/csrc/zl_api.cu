@@ -146,6 +146,11 @@ void free_plan(zl_plan_s* p) {
     cudaFree(p->t1);
     cudaFree(p->h_x);
     cudaFree(p->h_xt);
+    if (p->h_in) cudaStreamDestroy(p->h_in);
+    if (p->h_out) cudaStreamDestroy(p->h_out);
+    for (cudaEvent_t ev : {p->h_start, p->h_in_done[0], p->h_in_done[1], p->h_comp_done[0], p->h_comp_done[1],
+                           p->h_out_done[0], p->h_out_done[1]})
+        if (ev) cudaEventDestroy(ev);
     cudaFree(p->d_status);
     free_tables(p->td);
     free_tables(p->tf);
@@ -443,33 +448,79 @@ zl_status zl_apply_adjoint(zl_plan p, const void* y, void* g, int R, void* strea
     return run(p, Op::Adjoint, y, g, R, stream);
 }
 
+// Right-hand sides per piece of the host-buffer entry point: about a quarter of max_rhs,
+// in multiples of the tensor-core kernel's 16-rhs unit, at least 16 and at most max_rhs.
+static int host_piece(int max_rhs) {
+    const int q = ((max_rhs + 3) / 4 + 15) / 16 * 16;
+    return std::min(max_rhs, std::max(16, q));
+}
+
+static cudaError_t host_staging(zl_plan_s* p, size_t in_b, size_t out_b) {
+    if (p->h_x != nullptr) return cudaSuccess;
+    const int piece = host_piece(p->d.max_rhs);
+    cudaError_t e = cudaMalloc(&p->h_x, 2 * piece * in_b);
+    if (e == cudaSuccess) e = cudaMalloc(&p->h_xt, 2 * piece * out_b);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->h_in, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->h_out, cudaStreamNonBlocking);
+    for (cudaEvent_t* ev : {&p->h_start, &p->h_in_done[0], &p->h_in_done[1], &p->h_comp_done[0], &p->h_comp_done[1],
+                            &p->h_out_done[0], &p->h_out_done[1]})
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        cudaFree(p->h_x);
+        cudaFree(p->h_xt);
+        p->h_x = p->h_xt = nullptr;   // streams and events made so far are released with the plan
+        return e;
+    }
+    p->h_piece = piece;
+    return cudaSuccess;
+}
+
 zl_status zl_apply_left_inverse_host(zl_plan p, const void* x, void* xt, int R, void* stream) {
     if (!valid_plan(p) || R < 0 || (R > 0 && (x == nullptr || xt == nullptr))) return ZL_ERR_ARG;
     if (p->bad_column >= 0) return ZL_ERR_RANK;
     if (R == 0) return ZL_OK;
     cudaStream_t s = (cudaStream_t)stream;
     const size_t in_b = (size_t)p->d.nw * p->nh * p->esize, out_b = (size_t)p->d.K * p->L * p->esize;
-    const int chunk = p->d.max_rhs;
-    cudaError_t e = cudaSuccess;
-    if (p->h_x == nullptr) {
-        e = cudaMalloc(&p->h_x, in_b * chunk);
-        if (e == cudaSuccess) e = cudaMalloc(&p->h_xt, out_b * chunk);
-        if (e != cudaSuccess) {
-            cudaFree(p->h_x);
-            p->h_x = p->h_xt = nullptr;
-            return cuda_status(e);
-        }
+    cudaError_t e = host_staging(p, in_b, out_b);
+    if (e != cudaSuccess) return cuda_status(e);
+    const int piece = p->h_piece;
+    // Piece i uses staging slot i % 2: its copy-in (h_in) overlaps the kernels of piece i - 1
+    // (on `stream`) and the copy-out of piece i - 2 (h_out).  The copies of a call start after
+    // the work queued on `stream` before it.
+    zl_status st = ZL_OK;
+    e = cudaEventRecord(p->h_start, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(p->h_in, p->h_start, 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(p->h_out, p->h_start, 0);
+    for (int r0 = 0, i = 0; r0 < R && e == cudaSuccess && st == ZL_OK; r0 += piece, ++i) {
+        const int rc = std::min(piece, R - r0), b = i & 1;
+        char* dx = (char*)p->h_x + (size_t)b * piece * in_b;
+        char* dxt = (char*)p->h_xt + (size_t)b * piece * out_b;
+        // slot b of x was last read by the kernels of piece i - 2, slot b of x~ last copied out
+        // by piece i - 2
+        if (i >= 2) e = cudaStreamWaitEvent(p->h_in, p->h_comp_done[b], 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(dx, (const char*)x + (size_t)r0 * in_b, rc * in_b, cudaMemcpyHostToDevice, p->h_in);
+        if (e == cudaSuccess) e = cudaEventRecord(p->h_in_done[b], p->h_in);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, p->h_in_done[b], 0);
+        if (e == cudaSuccess && i >= 2) e = cudaStreamWaitEvent(s, p->h_out_done[b], 0);
+        if (e != cudaSuccess) break;
+        st = run(p, Op::LeftInverse, dx, dxt, rc, stream);
+        if (st != ZL_OK) break;
+        e = cudaEventRecord(p->h_comp_done[b], s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(p->h_out, p->h_comp_done[b], 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync((char*)xt + (size_t)r0 * out_b, dxt, rc * out_b, cudaMemcpyDeviceToHost, p->h_out);
+        if (e == cudaSuccess) e = cudaEventRecord(p->h_out_done[b], p->h_out);
     }
-    for (int r0 = 0; r0 < R; r0 += chunk) {
-        const int rc = std::min(chunk, R - r0);
-        e = cudaMemcpyAsync(p->h_x, (const char*)x + r0 * in_b, rc * in_b, cudaMemcpyHostToDevice, s);
-        if (e != cudaSuccess) return cuda_status(e);
-        const zl_status st = run(p, Op::LeftInverse, p->h_x, p->h_xt, rc, stream);
-        if (st != ZL_OK) return st;
-        e = cudaMemcpyAsync((char*)xt + r0 * out_b, p->h_xt, rc * out_b, cudaMemcpyDeviceToHost, s);
-        if (e != cudaSuccess) return cuda_status(e);
-    }
-    return cuda_status(cudaStreamSynchronize(s));
+    // on every path, nothing queued by this call is still running when it returns
+    const cudaError_t e_in = cudaStreamSynchronize(p->h_in);
+    const cudaError_t e_s = cudaStreamSynchronize(s);
+    const cudaError_t e_out = cudaStreamSynchronize(p->h_out);
+    if (st != ZL_OK) return st;
+    if (e != cudaSuccess) return cuda_status(e);
+    if (e_in != cudaSuccess) return cuda_status(e_in);
+    if (e_s != cudaSuccess) return cuda_status(e_s);
+    return cuda_status(e_out);
 }
 
 zl_status zl_destroy(zl_plan p) {

@@ -72,9 +72,14 @@ struct zl_plan_s {
     zl::Tables<double> td;
     zl::Tables<float> tf;
     zl::TcOperands* tc = nullptr;
-    // staging for zl_apply_left_inverse_host (allocated on first use)
+    // zl_apply_left_inverse_host (allocated on first use): two device staging slots of
+    // h_piece right-hand sides each for x and for x~, the copy-in and copy-out streams, and
+    // per slot the events "copied in", "kernels done", "copied out"
     void* h_x = nullptr;
     void* h_xt = nullptr;
+    int h_piece = 0;
+    cudaStream_t h_in = nullptr, h_out = nullptr;
+    cudaEvent_t h_start = nullptr, h_in_done[2] = {}, h_comp_done[2] = {}, h_out_done[2] = {};
     int* d_status = nullptr;
     mutable zl::StageTimer timer;
     // kernel choice (set by the batch autotuner; defaults = the built-in heuristics):
