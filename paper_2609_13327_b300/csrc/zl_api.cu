@@ -138,19 +138,29 @@ void free_tables(zl::Tables<T>& t) {
     t = zl::Tables<T>();
 }
 
+// Staging, streams and events of the host-buffer entry point (any subset may exist).
+void release_host_staging(zl_plan_s* p) {
+    cudaFree(p->h_x);
+    cudaFree(p->h_xt);
+    p->h_x = p->h_xt = nullptr;
+    if (p->h_in) cudaStreamDestroy(p->h_in);
+    if (p->h_out) cudaStreamDestroy(p->h_out);
+    p->h_in = p->h_out = nullptr;
+    for (cudaEvent_t* ev : {&p->h_start, &p->h_in_done[0], &p->h_in_done[1], &p->h_comp_done[0], &p->h_comp_done[1],
+                            &p->h_out_done[0], &p->h_out_done[1]}) {
+        if (*ev) cudaEventDestroy(*ev);
+        *ev = nullptr;
+    }
+    p->h_piece = 0;
+}
+
 void free_plan(zl_plan_s* p) {
     if (!p) return;
     zl::tc_release(*p);
     cudaFree(p->Zc);
     cudaFree(p->P);
     cudaFree(p->t1);
-    cudaFree(p->h_x);
-    cudaFree(p->h_xt);
-    if (p->h_in) cudaStreamDestroy(p->h_in);
-    if (p->h_out) cudaStreamDestroy(p->h_out);
-    for (cudaEvent_t ev : {p->h_start, p->h_in_done[0], p->h_in_done[1], p->h_comp_done[0], p->h_comp_done[1],
-                           p->h_out_done[0], p->h_out_done[1]})
-        if (ev) cudaEventDestroy(ev);
+    release_host_staging(p);
     cudaFree(p->d_status);
     free_tables(p->td);
     free_tables(p->tf);
@@ -466,9 +476,7 @@ static cudaError_t host_staging(zl_plan_s* p, size_t in_b, size_t out_b) {
                             &p->h_out_done[0], &p->h_out_done[1]})
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
     if (e != cudaSuccess) {
-        cudaFree(p->h_x);
-        cudaFree(p->h_xt);
-        p->h_x = p->h_xt = nullptr;   // streams and events made so far are released with the plan
+        release_host_staging(p);
         return e;
     }
     p->h_piece = piece;
