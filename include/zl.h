@@ -124,6 +124,9 @@ zl_status zl_get_info(zl_plan plan, int* L, int* nw, int* K, long long* nh, int*
  *   device_error      0, or the code the tensor-core kernel recorded when one
  *                     of its bounded waits timed out (the call then returns
  *                     ZL_ERR_TIMEOUT).  Reading it synchronises the device.
+ *                     The code stays recorded until zl_set_test_wait_timeout
+ *                     (plan, 0) clears it; the results of the applies queued
+ *                     since the timeout are undefined.
  */
 zl_status zl_get_runtime_info(zl_plan plan, int* tensor_core_path, int* device_error);
 
