@@ -12,14 +12,14 @@
  *   Z     the scaled ensemble z_k = (e_k - mean)/sqrt(K-1) (Sec. 3.3), stored
  *         [K][n_w][n_h]: member-major, then segment l, then column m (the
  *         segment ordering of Sec. 3.4).
- *   C_b   the n_h x n_h horizontal localization block (Sec. 3.5); every block
+ *   C_b   the n_h x n_h horizontal localization block (Sec. 3.6); every block
  *         of the localization equals C_b.  libzl accepts the localizations
  *         diagonalised by the packed real-Fourier basis of a periodic grid
  *         (circulant in 1-D, block-circulant with circulant blocks in 2-D,
  *         even in each axis): the caller gives their eigenvalues.
  *   Zh    = C^{1/2} (triangle) Z = A V Delta^{1/2}, the modulated-ensemble
- *         square root (Sec. 3.6, 3.8), n x K*L.
- *   Zh^-  = Delta^{-1/2} V^T A^{-1}, its left inverse (Sec. 3.8, Eq.
+ *         square root (Sec. 3.7, 3.9), n x K*L.
+ *   Zh^-  = Delta^{-1/2} V^T A^{-1}, its left inverse (Sec. 3.9, Eq.
  *         InverseSquareRootAlmost).  When n_w != K, A^{-1} is replaced by the
  *         pseudo-inverse A^+ = blockdiag over columns of A_m^+ (minimum norm
  *         for n_w < K, least squares for n_w > K); this is a genuine left
@@ -81,15 +81,15 @@ typedef struct {
 
 /*
  * zl_setup -- precompute everything the applies need (the paper's experiment
- * steps (a)-(e), Sec. 4.5, and the economical eigendecomposition of C_b,
- * Sec. 3.8).
+ * steps (a)-(e), Sec. 4.7, and the economical eigendecomposition of C_b,
+ * Sec. 3.9).
  *
  *   desc      sizes and precision (copied).
  *   Z         device, [K][nw][ny*nx], double (ZL_FP64) or float; read only
  *             during the call (libzl keeps its own copy).
  *   spectrum  host, [ny*nx] doubles: eigenvalue of C_b for every packed mode s,
  *             all finite, max > 0.  Modes with lambda_s <= tau*max are dropped
- *             ("non-zero eigenvalues", Sec. 3.8); L = number kept.
+ *             ("non-zero eigenvalues", Sec. 3.9); L = number kept.
  *   stream    queue for the setup work; the call synchronises it.
  *   out       receives the plan.  On ZL_OK and on ZL_ERR_RANK *out is a valid
  *             plan (on ZL_ERR_RANK every apply returns ZL_ERR_RANK; query the
@@ -152,7 +152,7 @@ zl_status zl_get_modes(zl_plan plan, int* modes);
 
 /*
  * zl_apply_left_inverse -- x~ = Zh^- x for R state vectors: steps V1-V5 of
- * Sec. 3.9.  V1: w^(m) = A_m^+ x^(m) for every column; V2-V3: regroup w into
+ * Sec. 3.10.  V1: w^(m) = A_m^+ x^(m) for every column; V2-V3: regroup w into
  * its K member segments; V4: x~_k = Delta_b^{-1/2} V_b^T w_k; V5: concatenate.
  *
  *   x    device, [R][nw][ny*nx] (segment order), read only.
@@ -178,7 +178,7 @@ zl_status zl_apply_left_inverse(zl_plan plan, const void* x, void* xt, int R, vo
 zl_status zl_apply_left_inverse_host(zl_plan plan, const void* x, void* xt, int R, void* stream);
 
 /*
- * zl_apply_sqrt -- x = Zh x~ = A V Delta^{1/2} x~ (Sec. 3.8):
+ * zl_apply_sqrt -- x = Zh x~ = A V Delta^{1/2} x~ (Sec. 3.9):
  * y_k = V_b Delta_b^{1/2} x~_k, then x^(m) = A_m y^(m) per column.
  *   xt device [R][K][L] read only;  x device [R][nw][ny*nx] written.
  */
@@ -292,7 +292,7 @@ zl_status zl_gaussian_spectrum(int nx, int ny, double ell, double* out);
 /* ------------------------------------------------------------------ batches
  * Many independent instances (each its own grid, n_w, K, localization and
  * number of right-hand sides) applied together.  The paper's algorithm runs
- * on each instance unchanged (Sec. 3.9); the batch is a property of this
+ * on each instance unchanged (Sec. 3.10); the batch is a property of this
  * library.
  */
 typedef struct zl_batch_s* zl_batch;   /* opaque; owned by libzl, freed by zl_destroy_batch */

@@ -10,21 +10,21 @@ only where the paper's own statement is "for each column m", and otherwise
 written as the definitions of Sardelli & Bishop (arxiv 2609.13327) read:
 
 * ``basis``  -- the localization's horizontal eigenbasis on a periodic grid
-  (economical eigendecomposition of C_b, Sec. 3.8) and the periodized-Gaussian
+  (economical eigendecomposition of C_b, Sec. 3.9) and the periodized-Gaussian
   spectrum with its closed form (Poisson summation).
-* ``swift``  -- the vector-form swift algorithm V1-V4 (Sec. 3.9) for the left
+* ``swift``  -- the vector-form swift algorithm V1-V4 (Sec. 3.10) for the left
   inverse, with the n_w != K generalisation A^{-1} -> A^+, and the square root
-  A V Delta^{1/2} (Sec. 3.8) and both adjoints.
+  A V Delta^{1/2} (Sec. 3.9) and both adjoints.
 * ``dense``  -- brute force at tiny sizes: the modulated square root
-  Zh = C^{1/2} (triangle) Z (Sec. 3.6), the matrix A (Sec. 3.6), its
+  Zh = C^{1/2} (triangle) Z (Sec. 3.7), the matrix A (Sec. 3.7), its
   pseudo-inverse by dense SVD, the dense left inverse Delta^{-1/2} V^T A^+
-  (Sec. 3.8, "InverseSquareRootSwift") and the accuracy indicators Xi and delta
-  (Sec. 4.6, 4.7).
+  (Sec. 3.9, "InverseSquareRootSwift") and the accuracy indicators Xi and delta
+  (Sec. 4.8, 4.9).
 
 Parity pins: every function is checked by ``tests/test_oracle_pins.py``
 against closed forms, brute force and the paper's identities.  The only
 "parity unpinned" quantities are the paper's reported accuracy numbers
-(RMSE_Xi, MAX_Xi, RMSE_delta of Sec. 4.6-4.7), whose inputs (spherical grid,
+(RMSE_Xi, MAX_Xi, RMSE_delta of Sec. 4.8-4.9), whose inputs (spherical grid,
 spherical-harmonics covariance and localization) the paper does not specify
 fully enough to rebuild.
 """

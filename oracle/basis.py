@@ -2,9 +2,9 @@
 
 TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
 
-Sec. 3.8 of the paper writes the localization block as an economical
+Sec. 3.9 of the paper writes the localization block as an economical
 eigendecomposition C_b = V_b Delta_b V_b^T, keeping only the columns of the
-orthogonal eigenvector matrix whose eigenvalue is non-zero; Sec. 3.10 notes
+orthogonal eigenvector matrix whose eigenvalue is non-zero; Sec. 3.11 notes
 that V_b can be generated analytically instead of stored.  On a doubly
 periodic grid with an even, separable correlation function the eigenvectors
 are the real Fourier modes, so the oracle fixes that basis explicitly:

@@ -12,8 +12,8 @@ Forms the paper's matrices explicitly, with state index i = l*n_h + m
 * V, Delta  block diagonal with K copies of V_b and Delta_b (Eq. VBlocks, DeltaBlocks)
 * Zh^-      Delta^{-1/2} V^T A^+ (Eq. InverseSquareRootAlmost with A^{-1} -> A^+,
             A^+ by dense SVD, i.e. ``numpy.linalg.pinv``)
-* Xi        I - Zh^- (Zh Zh^T) Zh^-^T and its two indicators (Sec. 4.6)
-* delta     x~ - Zh^- Zh x~ and its 2-norm (Sec. 4.7)
+* Xi        I - Zh^- (Zh Zh^T) Zh^-^T and its two indicators (Sec. 4.8)
+* delta     x~ - Zh^- Zh x~ and its 2-norm (Sec. 4.9)
 """
 
 import numpy as np
@@ -73,7 +73,7 @@ def xi_indicators(Zinv, Zh):
     """Xi = I - Zh^- Ph Zh^-^T with Ph = Zh Zh^T; returns (||Xi||_F, max |Xi_ij|).
 
     The paper calls the first one RMSE_Xi but defines it without a mean, i.e.
-    the Frobenius norm (Sec. 4.6); it is reported as such.
+    the Frobenius norm (Sec. 4.8); it is reported as such.
     """
     M = Zinv @ Zh
     Xi = np.eye(M.shape[0]) - M @ M.T
@@ -81,5 +81,5 @@ def xi_indicators(Zinv, Zh):
 
 
 def rmse_delta(Zinv, Zh, xt):
-    """||x~ - Zh^- Zh x~||_2 (Sec. 4.7; again a 2-norm, not a mean)."""
+    """||x~ - Zh^- Zh x~||_2 (Sec. 4.9; again a 2-norm, not a mean)."""
     return float(np.linalg.norm(xt - Zinv @ (Zh @ xt)))

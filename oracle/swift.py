@@ -2,16 +2,16 @@
 
 TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
 
-Notation follows the paper (Sec. 3.2-3.9):
+Notation follows the paper (Sec. 3.2-3.10):
   Z      ensemble, array [K][n_w][n_h]; member k is z_k, segment l is z_{l,k}
          (the segment ordering of Sec. 3.4), so z_k[l*n_h + m] = Z[k, l, m].
   A_m    the n_w x K matrix of the m-th grid vertical column, A_m[l, k] =
-         Z[k, l, m] (Sec. 3.8: Z with every row deleted except those of column m).
+         Z[k, l, m] (Sec. 3.9: Z with every row deleted except those of column m).
   x      a batch of state vectors, array [R][n_w][n_h] (same segment order).
-  xt     standardized variables x~ = Zh^- x, array [R][K][L] (Sec. 3.9, V5).
+  xt     standardized variables x~ = Zh^- x, array [R][K][L] (Sec. 3.10, V5).
 
 The paper assumes n_w = K so that every A_m is square and invertible
-(Sec. 3.7, Eq. nwEqualsK), and computes A_m^{-1} from the per-column singular
+(Sec. 3.8, Eq. nwEqualsK), and computes A_m^{-1} from the per-column singular
 value decomposition A_m = E_m Lambda_m F_m^T (Eq. svdOfAm; step V1 writes
 w^(m) = F_m Lambda_m^{-1} E_m^T x^(m)).  The oracle does exactly that with the
 thin SVD, which for n_w != K yields the pseudo-inverse
@@ -33,7 +33,7 @@ from . import basis as _basis
 
 
 class Plan:
-    """Everything the swift algorithm precomputes (experiment steps (a)-(e), Sec. 4.5)."""
+    """Everything the swift algorithm precomputes (experiment steps (a)-(e), Sec. 4.7)."""
 
     def __init__(self, Z, Nx, Ny, lam, tau, rank_eps=1e-13):
         Z = np.asarray(Z, dtype=np.float64)
@@ -166,7 +166,7 @@ def gram_route_pinv_apply(A, X, rank_eps=1e-13):
 # ---------------------------------------------------------------------------
 
 def apply_left_inverse(plan, x):
-    """x~ = Zh^- x = Delta^{-1/2} V^T A^+ x by steps V1-V5 (Sec. 3.9).
+    """x~ = Zh^- x = Delta^{-1/2} V^T A^+ x by steps V1-V5 (Sec. 3.10).
 
     V1: w^(m) = A_m^+ x^(m) for every column m;
     V2/V3: regroup w into its K segments w_k (one per member);
@@ -182,7 +182,7 @@ def apply_left_inverse(plan, x):
 
 
 def apply_sqrt(plan, xt):
-    """x = Zh x~ = A V Delta^{1/2} x~ (Sec. 3.8)."""
+    """x = Zh x~ = A V Delta^{1/2} x~ (Sec. 3.9)."""
     xt = np.asarray(xt, dtype=np.float64)
     y = inverse_transform(plan, xt * np.sqrt(plan.lamS))  # y_k = V_b Delta_b^{1/2} x~_k
     Y = np.transpose(y, (2, 1, 0))                      # [n_h][K][R]

@@ -1,9 +1,9 @@
 """torch.autograd wrappers of the library's operators (argument marshalling only).
 
-``left_inverse(plan, x)`` is x~ = Zh^- x (the vector algorithm V1-V5, Sec. 3.9) with its
+``left_inverse(plan, x)`` is x~ = Zh^- x (the vector algorithm V1-V5, Sec. 3.10) with its
 vector-Jacobian product (Zh^-)^T g computed by the library's adjoint kernels
 (``zl_apply_adjoint``), so a variational cost such as J(x) = 1/2 ||Zh^- x||^2 can be
-differentiated through it.  ``sqrt(plan, xt)`` is x = Zh x~ (Sec. 3.8, Zh = A V Delta^{1/2})
+differentiated through it.  ``sqrt(plan, xt)`` is x = Zh x~ (Sec. 3.9, Zh = A V Delta^{1/2})
 with its vector-Jacobian product Zh^T g (``zl_apply_sqrt_adjoint``).  Every computation
 runs in libzl's CUDA kernels; there is no fallback.
 """

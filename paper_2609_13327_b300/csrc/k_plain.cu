@@ -6,10 +6,10 @@
 // per-mode scale (Delta_b^{-1/2} or Delta_b^{1/2}):
 //
 //   forward  out[r][k][j] = scale_j * (V_b^T w_k)_{s_j},  w_k[m] = sum_l M[k][l][m] x[r][l][m]
-//            left inverse (M = P, Delta^{-1/2}): steps V1-V5 of Sec. 3.9
+//            left inverse (M = P, Delta^{-1/2}): steps V1-V5 of Sec. 3.10
 //            Zh^T         (M = Z, Delta^{+1/2})
 //   inverse  out[r][l][m] = sum_k M[k][l][m] y_k[m],  y_k = V_b (scale (.) c_k)
-//            square root  (M = Z, Delta^{+1/2}): A V Delta^{1/2} (Sec. 3.8)
+//            square root  (M = Z, Delta^{+1/2}): A V Delta^{1/2} (Sec. 3.9)
 //            adjoint      (M = P, Delta^{-1/2}): (A^+)^T V Delta^{-1/2}
 //
 // V_b^T is applied separably: an x-pass per grid row that keeps only the Px

@@ -1,8 +1,8 @@
 // Setup: the per-column pseudo-inverse A_m^+ in FP64 (one CTA per grid column).
 //
 // The paper factorises every column matrix A_m (n_w x K, A_m[l][k] = Z[k][l][m],
-// Sec. 3.8) by an SVD and applies A_m^{-1} = F_m Lambda_m^{-1} E_m^T in step V1
-// (Sec. 3.9).  Here the same operator is formed once per column as a dense
+// Sec. 3.9) by an SVD and applies A_m^{-1} = F_m Lambda_m^{-1} E_m^T in step V1
+// (Sec. 3.10).  Here the same operator is formed once per column as a dense
 // K x n_w matrix P_m = A_m^+ so that every apply is a single product:
 //
 //   1. Gram     G_m = A_m A_m^T (n_w <= K)  or  A_m^T A_m (n_w > K), g = min(n_w, K)

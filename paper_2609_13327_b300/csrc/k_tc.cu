@@ -2,7 +2,7 @@
 // persistent, warp-specialised tcgen05 kernel.
 //
 // Work unit = (grid row y, chunk of RC = 16 right-hand sides).  For every
-// column m of the row the per-column product of step V1 (Sec. 3.9),
+// column m of the row the per-column product of step V1 (Sec. 3.10),
 //     w^(m) = A_m^+ x^(m),   a K x n_w by n_w x RC product,
 // runs on the tensor cores with FP16 operand splits P = P_hi + P_lo and
 // x = x_hi + x_lo.  One MMA per K-step yields all four partial products: the A

@@ -1,6 +1,6 @@
 // Batched left inverse over many independent instances with uneven grids,
 // level counts, ensemble sizes and right-hand-side counts (the paper's
-// algorithm applies to each instance unchanged, Sec. 3.9; the instances share
+// algorithm applies to each instance unchanged, Sec. 3.10; the instances share
 // nothing).
 //
 // The batch owns one plan per instance.  An apply with a given set of buffers

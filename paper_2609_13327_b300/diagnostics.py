@@ -1,13 +1,13 @@
-"""Matrix-form accuracy diagnostics of a plan (the paper's Sec. 4.6-4.7 measures).
+"""Matrix-form accuracy diagnostics of a plan (the paper's Sec. 4.8-4.9 measures).
 
 * ``xi_indicators(plan)``: Xi = I - Zh^- (Zh Zh^T) Zh^-T, the deviation of the left
-  inverse from whitening the modulated-ensemble covariance P^ = Zh Zh^T (Sec. 4.6), and
+  inverse from whitening the modulated-ensemble covariance P^ = Zh Zh^T (Sec. 4.8), and
   its two indicators: the Frobenius norm (the paper's "RMSE_Xi", defined without a mean)
   and max |Xi_ij|.  M = Zh^- Zh is formed column by column on the GPU by the library's
   own kernels (the square root of every standardized unit vector, then the left
   inverse), in chunks of the plan's max_rhs; Xi = I - M M^T is one plain GEMM.  Memory
   and time grow as (K L)^2 and (K L)^3: meant for moderate sizes (K L of a few thousand).
-* ``delta(plan, xt)``: x~ - Zh^- Zh x~ per right-hand side and its 2-norm (Sec. 4.7).
+* ``delta(plan, xt)``: x~ - Zh^- Zh x~ per right-hand side and its 2-norm (Sec. 4.9).
 
 Every operator application runs in libzl's kernels; PyTorch supplies device memory and
 the one matrix product.

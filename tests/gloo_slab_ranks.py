@@ -5,7 +5,7 @@ rows y0 <= y < y1 of the ensemble and of the right-hand sides.  It computes V1 (
 column, Gram route) for its columns, the x-pass of its rows, and its share of the y-sum
 of V3, Sum_{y0 <= y < y1} b_{p_y}(y) (x-pass)[y, p_x], for the kept modes.  One all-reduce
 (sum) of the K L partial sums per right-hand side follows, then the Delta_b^{-1/2}
-scaling (V4).  V1 is independent per column (Sec. 3.9) and V3 is a sum over rows, so
+scaling (V4).  V1 is independent per column (Sec. 3.10) and V3 is a sum over rows, so
 the result must equal the whole-grid left inverse.  Rank 0 prints the relative error
 against the oracle's whole-grid apply.
 """

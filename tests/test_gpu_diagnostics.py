@@ -1,4 +1,4 @@
-"""Matrix-form diagnostics on the GPU (Xi indicators and delta, Sec. 4.6-4.7) against the
+"""Matrix-form diagnostics on the GPU (Xi indicators and delta, Sec. 4.8-4.9) against the
 oracle's dense brute force: Zh and Zh^- formed explicitly (dense SVD pseudo-inverse).
 
 With n_w < K and truncated modes, M = Zh^- Zh = Delta^{-1/2} V^T (A^+ A) V Delta^{1/2} is a

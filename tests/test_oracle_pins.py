@@ -141,7 +141,7 @@ def test_mode_counts_of_benchmark_shapes():
 
 @pytest.mark.parametrize("w", [SQUARE_RING, tiny("c0a_plane", ell_loc=1.0), WIDE, TALL], ids=lambda w: w.name)
 def test_sqrt_squares_to_localized_covariance(w):
-    """Zh Zh^T = (1 (x) C_b) (.) Z Z^T when no mode is dropped (Sec. 3.6)."""
+    """Zh Zh^T = (1 (x) C_b) (.) Z Z^T when no mode is dropped (Sec. 3.7)."""
     Z, lam, plan = make(w, tau=0.0, spectrum=lambda a, b, c: np.outer(basis.spectrum_1d_closed_form(b, c), basis.spectrum_1d_closed_form(a, c)).reshape(-1))
     assert plan.L == w.nh
     Zh = dense.modulated_sqrt(Z, w.Nx, w.Ny, lam, plan.S)
@@ -152,7 +152,7 @@ def test_sqrt_squares_to_localized_covariance(w):
 
 
 def test_sqrt_factorisation_A_V_Delta():
-    """Zh = A V Delta^{1/2} (Sec. 3.8)."""
+    """Zh = A V Delta^{1/2} (Sec. 3.9)."""
     w = SQUARE_PLANE
     Z, lam, plan = make(w)
     Zh = dense.modulated_sqrt(Z, w.Nx, w.Ny, lam, plan.S)
@@ -190,7 +190,7 @@ def test_swift_left_inverse_matches_dense_pinv(w):
 # ---------------------------------------------------------------- left inverse (P5, P6, P7)
 
 def test_left_inverse_property_square():
-    """Zh^- Zh = I and Xi ~ 0 when n_w = K (Sec. 4.6)."""
+    """Zh^- Zh = I and Xi ~ 0 when n_w = K (Sec. 4.8)."""
     for w in (SQUARE_RING, SQUARE_PLANE):
         Z, lam, plan = make(w)
         Zinv = dense.left_inverse_matrix(Z, w.Nx, w.Ny, lam, plan.S)
@@ -236,7 +236,7 @@ def test_right_inverse_when_wide_and_untruncated():
 
 
 def test_delta_indicator_paper_shape():
-    """The vector-form accuracy test of Sec. 4.7 at the paper's n_w = K = 64 column size.
+    """The vector-form accuracy test of Sec. 4.9 at the paper's n_w = K = 64 column size.
 
     delta = x~ - Zh^- Zh x~ for x~ ~ N(0, I), 50 draws per ensemble, three
     ensembles.  In floating point ||delta|| is bounded to first order by
