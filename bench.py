@@ -48,6 +48,8 @@ def parse_args():
     ap.add_argument("--prec", default=None, choices=["fp64", "fp32", "mixed"])
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fp64-steps", type=int, default=5,
+                    help="timed steps of the plain FP64 GPU form of the same workload (0: skip)")
     return ap.parse_args()
 
 
@@ -328,11 +330,31 @@ def run_ours(args, w, prec):
            "h2d_bytes_per_step": xh.numel() * xh.element_size(), "d2h_bytes_per_step": oh.numel() * oh.element_size(),
            "steps": args.e2e_steps, "api": "zl_apply_left_inverse_host (pinned host buffers)"}
 
+    # the host link alone: one pinned host -> device copy of a step's x (cudaMemcpyAsync), events
+    xd = torch.empty_like(x)
+    link_s = []
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        xd.copy_(xh, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        link_s.append(e0.elapsed_time(e1) / 1e3)
+    del xd
+    link_gbs = e2e["h2d_bytes_per_step"] / min(link_s) / 1e9
+    e2e["link_h2d_gbs"] = link_gbs
+    e2e["h2d_gbs_achieved"] = e2e["h2d_bytes_per_step"] * e2e["value"] / R / 1e9
+    e2e["frac_of_link"] = e2e["h2d_gbs_achieved"] / link_gbs
+
     clocks = ClockSampler.summarize(rows, t_wall0, t_wall1)
+    vs_fp64 = None
+    if prec != "fp64" and args.fp64_steps > 0:
+        vs_fp64 = fp64_gpu_form(w, R, rank, dev, args.fp64_steps, stream)
+        vs_fp64["ratio"] = value / world / vs_fp64["value"]
     line = {
         "metric": "left-inverse applications/s", "value": value, "unit": "vectors/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None,
+        "scaling": "weak", "vs_baseline": None, "vs_fp64_gpu": vs_fp64,
         "dtype": "f16x3 split, f32 accumulate" if (prec == "mixed" and plan_uses_tc(plan)) else
                  ("f64" if prec == "fp64" else "f32"),
         "data": "synthetic (seeded Gaussian-correlated ensemble, N(0,1) right-hand sides)",
@@ -355,6 +377,34 @@ def run_ours(args, w, prec):
     plan.destroy()
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def fp64_gpu_form(w, R, rank, dev, steps, stream):
+    """The plain FP64 GPU form of the same algorithm (ZL_FP64 plan, CUDA-core kernels) on the
+    same workload and right-hand sides, timed with CUDA events: the speedup denominator."""
+    import torch
+    from paper_2609_13327_b300 import zl
+    Z = torch.from_numpy(synth.ensemble(w)).to(dev)
+    lam = zl.zl_gaussian_spectrum(w.Nx, w.Ny, w.ell_loc)
+    plan = zl.zl_setup(Z, lam, tau=w.tau, prec="fp64", max_rhs=R, nx=w.Nx, ny=w.Ny)
+    del Z
+    x = torch.from_numpy(synth.rhs(w, R=R, seed=w.seed + 1000 * rank, dtype=np.float64)).to(dev)
+    out = torch.empty((R, w.K, plan.L), dtype=torch.float64, device=dev)
+    for _ in range(2):
+        zl.zl_apply_left_inverse(plan, x, out, stream)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(steps):
+        zl.zl_apply_left_inverse(plan, x, out, stream)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / steps
+    plan.destroy()
+    del x, out
+    torch.cuda.empty_cache()
+    return {"value": R / (ms / 1e3), "unit": "vectors/s", "ms_per_step": ms, "steps": steps,
+            "what": "ZL_FP64 plan (FP64 CUDA-core kernels) on the same workload, this GPU; ratio = value / this"}
 
 
 def plan_uses_tc(plan):

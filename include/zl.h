@@ -91,6 +91,8 @@ typedef struct {
  *             all finite, max > 0.  Modes with lambda_s <= tau*max are dropped
  *             ("non-zero eigenvalues", Sec. 3.9); L = number kept.
  *   stream    queue for the setup work; the call synchronises it.
+ *             A tau for which no mode is kept (L = 0, e.g. tau >= 1) is
+ *             rejected with ZL_ERR_SHAPE before any device work.
  *   out       receives the plan.  On ZL_OK and on ZL_ERR_RANK *out is a valid
  *             plan (on ZL_ERR_RANK every apply returns ZL_ERR_RANK; query the
  *             first rank-deficient column with zl_get_info, then zl_destroy).
@@ -253,18 +255,22 @@ zl_status zl_get_stage_times(zl_plan plan, int stage, int* launches, double* tot
  * device memory is owned by another framework's pool.  This call allocates
  * nothing.  The paper has no counterpart; it is a property of this library.
  *
- * It runs the CUDA-core kernels (for ZL_MIXED plans too) and keeps the
- * intermediate of the separable transform in a 16 MiB scratch array compiled
- * into libzl, held by every GPU that loads the library until the process
- * exits.  Right-hand sides are processed in passes of at most
- * 16 MiB / (K * ny * Px * element size) of them (and at most max_rhs); a plan
- * for which even one right-hand side needs more than 16 MiB
- * (K * ny * Px * element size > 16 MiB, Px = kept x-frequencies) is rejected
- * with ZL_ERR_SHAPE before any work is queued.
+ * It runs the CUDA-core kernels (for ZL_MIXED plans too, on the FP32
+ * pseudo-inverse: FP32 accuracy) and keeps the intermediate of the separable
+ * transform in a 16 MiB scratch array compiled into libzl.  Right-hand sides
+ * are processed in passes of at most 16 MiB / (K * ny * Px * element size) of
+ * them (and at most max_rhs); a plan for which even one right-hand side needs
+ * more than 16 MiB (K * ny * Px * element size > 16 MiB, Px = kept
+ * x-frequencies) is rejected with ZL_ERR_SHAPE before any work is queued.
  *
- * The first call on a device looks up the scratch array's device address
- * (with that device current) and caches it; make that first call before any
- * stream capture.  Every call, on every stream, shares the one array, so calls
+ * The array exists on a device once the driver has loaded libzl's module
+ * holding it there.  zl_setup looks up the array's device address on the
+ * plan's device (which loads that module, under lazy module loading too) and
+ * loads every kernel this entry point launches, so from the first zl_setup on
+ * a device the 16 MiB stay reserved there until the process exits, and this
+ * call neither allocates nor loads anything: it only launches kernels.  If
+ * the array cannot be created (device memory full), zl_setup returns
+ * ZL_ERR_ALLOC.  Every call, on every stream, shares the one array, so calls
  * that overlap on the GPU race: serialise them (one stream, or events).
  * Nothing in the array needs clearing between calls: each pass overwrites the
  * part it reads.

@@ -614,6 +614,24 @@ cudaError_t forward_plain_on(const zl_plan_s& p, const Tables<T>& t, const T* M,
     return launch_ypass<T>(p, t1, p.Px, t.by, t.m_py, t.m_jx, scale, out, R, s, &t);
 }
 
+template <typename T>
+cudaError_t preload_forward_plain() {
+    cudaFuncAttributes a;
+    const void* fns[] = {
+        (const void*)fwd_column_xpass<T, 1>, (const void*)fwd_column_xpass<T, 2>, (const void*)fwd_column_xpass<T, 4>,
+        (const void*)fwd_column_xpass<T, 8>, (const void*)fwd_ypass_gemm<T, 8>, (const void*)fwd_ypass_gemm<T, 16>,
+        (const void*)fwd_ypass_gemm<T, 24>, (const void*)fwd_ypass_gemm<T, 32>, (const void*)fwd_ypass_gemm<T, 40>,
+        (const void*)fwd_ypass_gemm<T, 48>, (const void*)fwd_ypass_gemm<T, 64>, (const void*)fwd_ypass<T>};
+    for (const void* f : fns) {
+        const cudaError_t e = cudaFuncGetAttributes(&a, f);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+template cudaError_t preload_forward_plain<double>();
+template cudaError_t preload_forward_plain<float>();
+
 template cudaError_t forward_plain_on<double>(const zl_plan_s&, const Tables<double>&, const double*, const double*,
                                               const double*, double*, int, cudaStream_t, double*);
 template cudaError_t forward_plain_on<float>(const zl_plan_s&, const Tables<float>&, const float*, const float*,

@@ -343,6 +343,10 @@ zl_status zl_setup(const zl_desc* desc, const void* Z, const double* spectrum, v
             lamS.push_back(spectrum[s]);
         }
     p->L = (int)p->modes.size();
+    if (p->L == 0) {   // tau >= 1: no eigenvalue exceeds tau * max, so there is nothing to apply
+        delete p;
+        return ZL_ERR_SHAPE;
+    }
     std::vector<char> used(d.nx, 0);
     for (int s : p->modes) used[s % d.nx] = 1;
     std::vector<int> xfreq;
@@ -364,6 +368,10 @@ zl_status zl_setup(const zl_desc* desc, const void* Z, const double* spectrum, v
         return ZL_ERR_SHAPE;
     }
 
+    if (cudaGetDevice(&p->device) != cudaSuccess) {
+        delete p;
+        return ZL_ERR_CUDA;
+    }
     cudaStream_t s = (cudaStream_t)stream;
     const size_t mbytes = (size_t)d.K * d.nw * nh * p->esize;
     const size_t tbytes = (size_t)d.max_rhs * d.K * d.ny * p->Px * p->esize;
@@ -400,6 +408,14 @@ zl_status zl_setup(const zl_desc* desc, const void* Z, const double* spectrum, v
             free_plan(p);
             return ts;
         }
+    }
+    // the allocation-free entry point: its scratch array's address on this device (which
+    // loads the module that holds the array) and the kernels it launches, so that it loads
+    // and allocates nothing itself
+    const zl_status ss = zl::static_scratch_prepare(*p);
+    if (ss != ZL_OK) {
+        free_plan(p);
+        return ss;
     }
     *out = p;
     return ZL_OK;

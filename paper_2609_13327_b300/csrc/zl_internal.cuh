@@ -53,6 +53,7 @@ struct StageTimer {
 
 struct zl_plan_s {
     zl_desc d;
+    int device = 0;         // the CUDA device current at setup
     long long nh = 0;
     int g = 0;              // min(nw, K)
     int L = 0;              // kept modes
@@ -112,6 +113,14 @@ cudaError_t forward_plain_on(const zl_plan_s& p, const Tables<T>& t, const T* M,
 template <typename T>
 cudaError_t inverse_plain(const zl_plan_s& p, const Tables<T>& t, const T* M, const T* scale, const T* c, T* out,
                           int R, cudaStream_t s);
+
+// Loads every kernel forward_plain_on<T> can launch (cudaFuncGetAttributes), so that a
+// later launch loads no module code under lazy module loading.
+template <typename T>
+cudaError_t preload_forward_plain();
+
+// zl_static.cu: the allocation-free entry point's scratch address on p.device, and its kernels
+zl_status static_scratch_prepare(const zl_plan_s& p);
 
 // y-pass of the forward transform on an FP32 intermediate with row stride ldp
 cudaError_t forward_ypass_f32(const zl_plan_s& p, const float* t1, int ldp, const float* scale, float* out, int R,

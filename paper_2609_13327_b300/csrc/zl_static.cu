@@ -4,10 +4,13 @@
 //
 // The scratch holds the intermediate of the separable transform (the x-pass
 // output, R * K * ny * Px elements per pass).  It is a file-scope device array
-// of kStaticScratchBytes, so every GPU that loads libzl holds it until the
-// process exits.  Host code cannot use the array's name as a device address:
-// the address is looked up once per device with cudaGetSymbolAddress, with
-// that device current, on the first call made on it.
+// of kStaticScratchBytes.  Host code cannot use the array's name as a device
+// address: zl_setup looks the address up with cudaGetSymbolAddress on the
+// plan's device (that device current), which also makes the driver load the
+// module holding the array there (under lazy module loading, the array takes
+// device memory from that moment until the process exits).  zl_setup also
+// loads every kernel this entry point may launch, so the entry point itself
+// loads and allocates nothing: it only launches kernels.
 
 #include "zl_internal.cuh"
 
@@ -23,24 +26,27 @@ constexpr int kMaxDevices = 64;
 std::mutex g_scratch_mu;
 void* g_scratch_addr[kMaxDevices] = {};
 
-// Device address of g_static_scratch on the current device (looked up once per device).
-cudaError_t scratch_address(void** out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (g_scratch_addr[dev] == nullptr) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_static_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_addr[dev] = p;
+}  // namespace
+
+namespace zl {
+
+zl_status static_scratch_prepare(const zl_plan_s& p) {
+    if (p.device < 0 || p.device >= kMaxDevices) return ZL_ERR_UNSUPPORTED;
+    {
+        std::lock_guard<std::mutex> lock(g_scratch_mu);
+        if (g_scratch_addr[p.device] == nullptr) {
+            void* a = nullptr;
+            const cudaError_t e = cudaGetSymbolAddress(&a, g_static_scratch);
+            if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? ZL_ERR_ALLOC : ZL_ERR_CUDA;
+            g_scratch_addr[p.device] = a;
+        }
     }
-    *out = g_scratch_addr[dev];
-    return cudaSuccess;
+    const cudaError_t e = p.d.prec == ZL_FP64 ? preload_forward_plain<double>() : preload_forward_plain<float>();
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? ZL_ERR_ALLOC : ZL_ERR_CUDA;
+    return ZL_OK;
 }
 
-}  // namespace
+}  // namespace zl
 
 extern "C" zl_status zl_apply_left_inverse_static(zl_plan p, const void* x, void* xt, int R, void* stream) {
     if (p == nullptr || p->P == nullptr || R < 0 || (R > 0 && (x == nullptr || xt == nullptr))) return ZL_ERR_ARG;
@@ -49,10 +55,14 @@ extern "C" zl_status zl_apply_left_inverse_static(zl_plan p, const void* x, void
     if (x == xt) return ZL_ERR_ARG;
     // every element of the scratch is written by the x-pass before the y-pass reads it: nothing to clear
     const size_t per_rhs = (size_t)p->d.K * p->d.ny * p->Px * p->esize;
-    if (per_rhs > kStaticScratchBytes) return ZL_ERR_SHAPE;
+    if (per_rhs == 0 || per_rhs > kStaticScratchBytes) return ZL_ERR_SHAPE;
     const int chunk = (int)std::min<size_t>({kStaticScratchBytes / per_rhs, (size_t)p->d.max_rhs, (size_t)65535});
     void* scratch = nullptr;
-    if (scratch_address(&scratch) != cudaSuccess) return ZL_ERR_CUDA;
+    {
+        std::lock_guard<std::mutex> lock(g_scratch_mu);
+        if (p->device >= 0 && p->device < kMaxDevices) scratch = g_scratch_addr[p->device];
+    }
+    if (scratch == nullptr) return ZL_ERR_CUDA;   // zl_setup resolves it for every plan it returns
     cudaStream_t s = (cudaStream_t)stream;
     const long long in_len = (long long)p->d.nw * p->nh, out_len = (long long)p->d.K * p->L;
     for (int r0 = 0; r0 < R; r0 += chunk) {

@@ -124,3 +124,22 @@ def test_wait_timeout_hook_rejects_bad_arguments(zl):
     lib = zl._lib
     assert lib.zl_set_test_wait_timeout(None, 1) == zl.ZL_ERR_ARG
     assert lib.zl_set_test_wait_timeout(None, 0) == zl.ZL_ERR_ARG
+
+
+def test_setup_rejects_a_threshold_that_keeps_no_mode(zl):
+    """tau >= 1: no eigenvalue exceeds tau * max, L would be 0 (nothing to apply, and
+    per-mode sizes of zero).  Rejected as a shape error before any device work."""
+    lib = zl._lib
+    spec = np.linspace(1.0, 2.0, 16)
+    sp = spec.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    h = ctypes.c_void_p(123)
+    fake = ctypes.c_void_p(0x1000)   # never dereferenced: validation fails first
+    for prec in (zl.ZL_FP64, zl.ZL_FP32, zl.ZL_MIXED):
+        for tau in (1.0, 2.5):
+            d = zl.zl_desc(16, 1, 2, 4, prec, tau, 8)
+            assert lib.zl_setup(ctypes.byref(d), fake, sp, None, ctypes.byref(h)) == zl.ZL_ERR_SHAPE
+            assert h.value is None
+
+
+def test_static_entry_point_rejects_null_plan(zl):
+    assert zl._lib.zl_apply_left_inverse_static(None, None, None, 4, None) == zl.ZL_ERR_ARG

@@ -18,7 +18,7 @@ Zh of the oracle.
 import numpy as np
 import pytest
 
-from oracle import basis, dense, swift
+from oracle import basis, compare, dense, swift
 from paper_2609_13327_b300 import synth
 
 torch = pytest.importorskip("torch")
@@ -53,10 +53,6 @@ def dense_left_inverse(oracle, w):
     return cols.reshape(n, -1).T
 
 
-def rel(a, b):
-    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
-
-
 @pytest.mark.parametrize("prec,tol", [("fp32", 1e-5), ("fp64", 1e-10)])
 def test_gradient_matches_dense_transpose(mods, prec, tol):
     zl, ag = mods
@@ -69,8 +65,8 @@ def test_gradient_matches_dense_transpose(mods, prec, tol):
     Zinv = dense_left_inverse(oracle, SUB)
     xs = x.detach().cpu().numpy().astype(np.float64).reshape(SUB.R, -1)
     g_ref = (Zinv.T @ (Zinv @ xs.T)).T
-    assert rel(x.grad.cpu().numpy().astype(np.float64).reshape(SUB.R, -1), g_ref) <= tol
-    assert rel(xt.detach().cpu().numpy().astype(np.float64).reshape(SUB.R, -1), (Zinv @ xs.T).T) <= tol
+    compare.check(x.grad.cpu().numpy(), g_ref.reshape(SUB.R, SUB.nw, SUB.nh), tol, 1, f"gradient {prec}")
+    compare.check(xt.detach().cpu().numpy(), (Zinv @ xs.T).T.reshape(SUB.R, SUB.K, -1), tol, 2, f"forward {prec}")
 
 
 def test_gradient_central_differences(mods):
@@ -114,8 +110,9 @@ def test_sqrt_wrapper_matches_dense_zh(mods):
     x = ag.sqrt(plan, xt)
     (0.5 * (x ** 2).sum()).backward()
     xts = xt.detach().cpu().numpy().reshape(SUB.R, -1)
-    assert rel(x.detach().cpu().numpy().reshape(SUB.R, -1), (Zh @ xts.T).T) <= 1e-10
-    assert rel(xt.grad.cpu().numpy().reshape(SUB.R, -1), (Zh.T @ (Zh @ xts.T)).T) <= 1e-10
+    compare.check(x.detach().cpu().numpy(), (Zh @ xts.T).T.reshape(SUB.R, SUB.nw, SUB.nh), 1e-10, 1, "sqrt")
+    compare.check(xt.grad.cpu().numpy(), (Zh.T @ (Zh @ xts.T)).T.reshape(SUB.R, SUB.K, -1), 1e-10, 2,
+                  "sqrt gradient")
 
 
 def test_full_size_gradient_sampled(mods):
@@ -128,4 +125,4 @@ def test_full_size_gradient_sampled(mods):
     assert plan.device_error() == 0
     xs = x.detach()[[5]].cpu().numpy().astype(np.float64)
     g_ref = swift.apply_adjoint(oracle, swift.apply_left_inverse(oracle, xs))
-    assert rel(x.grad[[5]].cpu().numpy().astype(np.float64), g_ref) <= 1e-5
+    compare.check(x.grad[[5]].cpu().numpy(), g_ref, 1e-5, 1, "512x512x16 gradient")

@@ -11,7 +11,7 @@ results, and instances with no right-hand sides are skipped.
 import numpy as np
 import pytest
 
-from oracle import basis, swift
+from oracle import basis, compare, swift
 from paper_2609_13327_b300 import synth
 
 torch = pytest.importorskip("torch")
@@ -35,12 +35,6 @@ def instances(count):
     return [ws[i] for i in pick]
 
 
-def rel_err(out, ref):
-    out = out.reshape(len(out), -1)
-    ref = ref.reshape(len(ref), -1)
-    return float(np.max(np.linalg.norm(out - ref, axis=1) / np.linalg.norm(ref, axis=1)))
-
-
 @pytest.fixture(scope="module")
 def batch(zl):
     ws = instances(10)
@@ -62,7 +56,7 @@ def test_batch_matches_oracle_per_instance(zl, batch):
     for i, (w, o, x) in enumerate(zip(ws, outs, xs)):
         assert b.plans[i].device_error() == 0
         ref = swift.apply_left_inverse(oracles[i], x.astype(np.float64))
-        assert rel_err(o.cpu().numpy().astype(np.float64), ref) <= TOL_MIXED, (i, w, b.variants[i])
+        compare.check(o.cpu().numpy(), ref, TOL_MIXED, 2, f"instance {i} {w} variant {b.variants[i]}")
 
 
 def test_graph_replay_and_recapture(zl, batch):
@@ -88,7 +82,7 @@ def test_instances_without_rhs_are_skipped(zl, batch):
     torch.cuda.synchronize()
     assert outs[1].shape[0] == 0 and outs[3].shape[0] == 0
     ref = swift.apply_left_inverse(oracles[2], xs[2].astype(np.float64))
-    assert rel_err(outs[2].cpu().numpy().astype(np.float64), ref) <= TOL_MIXED
+    compare.check(outs[2].cpu().numpy(), ref, TOL_MIXED, 2, "instance 2")
 
 
 def test_each_plan_alone_equals_the_batch(zl, batch):

@@ -7,6 +7,7 @@ identity the paper states.  Sizes are tiny so the whole file runs in seconds.
 
 import dataclasses
 
+import mpmath   # a hard requirement: the spectrum pin below must not skip silently
 import numpy as np
 import pytest
 
@@ -73,7 +74,6 @@ def test_spectrum_closed_form(N, ell):
 def test_spectrum_relative_accuracy_at_the_threshold(N, ell):
     """Every eigenvalue above tau = 1e-10 (relative) to 1e-13 relative, against the definition
     evaluated with 50 significant digits; the FP64 direct sum misses this for the smallest."""
-    mpmath = pytest.importorskip("mpmath")
     mpmath.mp.dps = 50
     P = int(np.ceil(12.0 * ell / N)) + 6
     den = mpmath.fsum(mpmath.exp(-mpmath.mpf(p * N) ** 2 / (2 * mpmath.mpf(ell) ** 2)) for p in range(-P, P + 1))
@@ -199,6 +199,57 @@ def test_left_inverse_property_square():
         assert np.abs(M - np.eye(len(M))).max() < 1e-7
         fro, mx = dense.xi_indicators(Zinv, Zh)
         assert mx < 1e-7
+
+
+@pytest.mark.parametrize("w,tau", [(WIDE, 0.0), (WIDE, 1e-2), (SQUARE_PLANE, 1e-3)], ids=["wide", "wide_tau", "square_tau"])
+def test_xi_indicators_literal_definition(w, tau):
+    """Xi = I - Zh^- Ph Zh^-^T with Ph the localized sample covariance (Sec. 4.8, Eq.
+    MatrixDifferenceSwiftAlgorithm), formed without Zh: Ph = (1 (x) C_tau) (.) (Z Z^T) with
+    C_tau = V_b Delta_b V_b^T of the kept modes (= C_b when tau = 0).  For n_w < K the
+    product M = Zh^- Zh is not normal (M M^T != M^T M) and Xi is far from zero, so a
+    transposed product or a norm over the wrong axis fails here."""
+    Z, lam, plan = make(w, tau=tau)
+    S = plan.S
+    Vb = basis.basis_2d(w.Nx, w.Ny)[:, S]
+    Ct = (Vb * lam[S][None, :]) @ Vb.T
+    if tau == 0.0:
+        assert np.abs(Ct - basis.localization_block(w.Nx, w.Ny, w.ell_loc)).max() < 1e-12
+    Zm = np.asarray(Z, dtype=np.float64).reshape(w.K, -1).T          # n x K, member columns
+    Ph = np.kron(np.ones((w.nw, w.nw)), Ct) * (Zm @ Zm.T)
+    Zinv = dense.left_inverse_matrix(Z, w.Nx, w.Ny, lam, S)
+    Xi = np.eye(Zinv.shape[0]) - Zinv @ Ph @ Zinv.T
+    fro, mx = dense.xi_indicators(Zinv, dense.modulated_sqrt(Z, w.Nx, w.Ny, lam, S))
+    ref_fro, ref_mx = float(np.sqrt(np.sum(Xi ** 2))), float(np.max(np.abs(Xi)))
+    if w.nw == w.K:                    # Xi vanishes; the two routes agree to their rounding
+        assert fro < 1e-6 and ref_fro < 1e-6 and mx < 1e-6 and ref_mx < 1e-6
+        return
+    assert abs(fro - ref_fro) <= 1e-10 * max(ref_fro, 1.0)
+    assert abs(mx - ref_mx) <= 1e-10 * max(ref_mx, 1.0)
+    if w.nw < w.K:
+        assert ref_fro > 1.0 and ref_mx > 0.1                       # a genuinely non-zero Xi
+        M = Zinv @ dense.modulated_sqrt(Z, w.Nx, w.Ny, lam, S)
+        assert np.abs(M @ M.T - M.T @ M).max() > 1e-3                # the transposed product differs
+
+
+@pytest.mark.parametrize("w", [WIDE, TALL, SQUARE_PLANE], ids=lambda w: w.name)
+def test_rmse_delta_matches_the_vector_algorithm(w):
+    """||x~ - Zh^- Zh x~||_2 (Sec. 4.9, Eq. RMSEdelta) from the dense matrices equals the
+    same quantity from the vector algorithm (apply_sqrt, then apply_left_inverse); for
+    n_w < K it is far from zero, for n_w >= K it vanishes to rounding."""
+    Z, lam, plan = make(w)
+    Zinv = dense.left_inverse_matrix(Z, w.Nx, w.Ny, lam, plan.S)
+    Zh = dense.modulated_sqrt(Z, w.Nx, w.Ny, lam, plan.S)
+    xt = synth.coefficients(w, plan.L, R=3)
+    for r in range(3):
+        got = dense.rmse_delta(Zinv, Zh, xt[r].reshape(-1))
+        back = swift.apply_left_inverse(plan, swift.apply_sqrt(plan, xt[r:r + 1]))
+        ref = float(np.linalg.norm(xt[r] - back[0]))
+        scale = float(np.linalg.norm(xt[r]))
+        assert abs(got - ref) <= 1e-9 * scale
+        if w.nw < w.K:
+            assert ref > 0.1 * scale
+        else:
+            assert ref < 1e-8 * scale
 
 
 def test_left_inverse_equals_pinv_on_range():

@@ -4,20 +4,23 @@ Some callers cannot allocate device memory at the moment they apply the
 operator (a real-time loop with a memory budget fixed at start-up, a host
 callback, a process whose device memory belongs to another framework's pool).
 For them the library keeps the transform's intermediate in a static device
-array.  This file is collected last so a failure here comes after every other
-test has run; it passes alone in a fresh process as well as after the rest.
+array; zl_setup resolves the array's address and loads the kernels, so an
+apply only launches kernels.  This file is collected last so a failure here
+comes after every other test has run; it passes alone in a fresh process as
+well as after the rest.
 """
 
 import numpy as np
 import pytest
 
-from oracle import basis
+from oracle import basis, swift
 from paper_2609_13327_b300 import synth
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-10, "fp32": 1e-6}
+# the static path runs the CUDA-core kernels: FP32 accuracy for FP32 and mixed plans
+TOL = {"fp64": 1e-10, "fp32": 1e-6, "mixed": 1e-6}
 
 
 @pytest.fixture(scope="module")
@@ -37,20 +40,34 @@ def rel_err(out, ref):
 CASES = [
     (synth.WORKLOADS["c2_128x128x10"], "fp32", 64),     # 442 KB per rhs: two passes through the 16 MiB array
     (synth.Workload("ragged_fp64", 40, 24, 6, 9, 4.0, 0.6, 3.0, 7, "fp64", 61), "fp64", 7),
+    # a mixed plan (its own apply runs the tensor-core kernel): the static path uses the FP32 kernels
+    (synth.Workload("ragged_mixed", 48, 40, 32, 64, 8.0, 0.8, 6.0, 13, "mixed", 31, var_range=(0.1, 10.0)),
+     "mixed", 13),
 ]
 
 
 @pytest.mark.parametrize("w,prec,R", CASES, ids=[f"{w.name}-{p}" for w, p, _ in CASES])
-def test_static_scratch_matches_workspace_entry_point(zl, w, prec, R):
+def test_static_scratch_matches_workspace_entry_point_and_oracle(zl, w, prec, R):
     dt = synth.storage_dtype(prec)
     Z = synth.ensemble(w).astype(dt)
     lam = basis.spectrum_2d(w.Nx, w.Ny, w.ell_loc)
     plan = zl.zl_setup(torch.from_numpy(Z).cuda(), lam, tau=w.tau, prec=prec, max_rhs=R, nx=w.Nx, ny=w.Ny)
     x = torch.from_numpy(synth.rhs(w, R=R, dtype=dt)).cuda()
-    ref = zl.zl_apply_left_inverse(plan, x).cpu().numpy().astype(np.float64)
-    for _ in range(2):   # the array keeps the previous call's contents: a second call must not depend on them
-        out = zl.zl_apply_left_inverse_static(plan, x).cpu().numpy().astype(np.float64)
-        assert rel_err(out, ref) <= TOL[prec]
+    ref_ws = zl.zl_apply_left_inverse(plan, x).cpu().numpy().astype(np.float64)
+    oracle = swift.Plan(Z.astype(np.float64), w.Nx, w.Ny, lam, w.tau)
+    ref = swift.apply_left_inverse(oracle, x.cpu().numpy().astype(np.float64))
+    outs = [torch.empty((R, plan.K, plan.L), dtype=x.dtype, device="cuda") for _ in range(2)]
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for out in outs:   # the array keeps the previous call's contents: a second call must not depend on them
+        zl.zl_apply_left_inverse_static(plan, x, out)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0          # nothing allocated, no module loaded
+    tol_ws = TOL[prec] if prec != "mixed" else 1e-5       # the workspace path of a mixed plan is the tensor-core one
+    for out in outs:
+        got = out.cpu().numpy().astype(np.float64)
+        assert rel_err(got, ref) <= TOL[prec]
+        assert rel_err(got, ref_ws) <= tol_ws
 
 
 def test_static_scratch_rejects_plans_beyond_its_size(zl):
