@@ -147,7 +147,7 @@ def test_tensor_core_square_and_tall_columns(zl, w):
     compare.check(out, swift.apply_left_inverse(oracle, x.astype(np.float64)), TOL_MIXED, 2, w.name)
     # left-inverse property
     xt0 = synth.coefficients(w, plan.L)
-    xr = swift.apply_sqrt(oracle, xt0).astype(np.float32)
+    xr = np.ascontiguousarray(swift.apply_sqrt(oracle, xt0), dtype=np.float32)
     back = zl.zl_apply_left_inverse(plan, torch.from_numpy(xr).cuda()).cpu().numpy().astype(np.float64)
     ref = swift.apply_left_inverse(oracle, xr.astype(np.float64))
     e_or = np.linalg.norm((ref - xt0).reshape(w.R, -1), axis=1)
