@@ -164,6 +164,35 @@ zl_status zl_get_modes(zl_plan plan, int* modes);
 zl_status zl_apply_left_inverse(zl_plan plan, const void* x, void* xt, int R, void* stream);
 
 /*
+ * zl_apply_left_inverse_rows -- one slab's share of the left inverse, for a
+ * horizontal domain split into slabs of grid rows (the paper's parallel
+ * decomposition, Sec. 3.10: steps V1-V3 need only the slab's own columns, and
+ * V4's transform along y is a sum over rows).  For the rows y0 .. y1 - 1:
+ *   partial[r][k][j] = sum_{y in [y0, y1)} b_{p_y(j)}(y) * c_k(y, p_x(j)),
+ *   c_k(y, .) = the x-pass (V_b^T along x) of w_k = A^+ x on grid row y,
+ * i.e. x~ without the Delta^{-1/2} scaling.  The sum of the partials of slabs
+ * that cover the grid (one all-reduce of K L values per right-hand side when
+ * the slabs live on different GPUs), scaled by zl_scale_modes, is
+ * zl_apply_left_inverse's result.
+ *
+ *   y0, y1   0 <= y0 < y1 <= ny, else ZL_ERR_SHAPE
+ *   x        device, [R][nw][(y1 - y0) * nx]: the slab's rows of every segment
+ *            (the rows a rank holding the slab stores), read only
+ *   partial  device, [R][K][L], written
+ * Same kernels, precision and passes of max_rhs as zl_apply_left_inverse.
+ */
+zl_status zl_apply_left_inverse_rows(zl_plan plan, int y0, int y1, const void* x, void* partial, int R,
+                                     void* stream);
+
+/*
+ * zl_scale_modes -- xt[r][k][j] = lambda_j^{-1/2} partial[r][k][j] (step V4's
+ * Delta_b^{-1/2}), completing the sum of slab partials of
+ * zl_apply_left_inverse_rows.  partial and xt: device [R][K][L]; they may be
+ * the same buffer.
+ */
+zl_status zl_scale_modes(zl_plan plan, const void* partial, void* xt, int R, void* stream);
+
+/*
  * zl_apply_left_inverse_host -- the same operator on HOST buffers: copies x to
  * the device, applies, copies x~ back, and synchronises `stream`.  x and xt
  * should be page-locked for the copies to be asynchronous.  The right-hand
@@ -276,6 +305,54 @@ zl_status zl_get_stage_times(zl_plan plan, int stage, int* launches, double* tot
  * part it reads.
  */
 zl_status zl_apply_left_inverse_static(zl_plan plan, const void* x, void* xt, int R, void* stream);
+
+/* ------------------------------------------------------------ diagnostics
+ * The matrix-form and vector-form accuracy measures of the paper's experiment
+ * (Sec. 4.7-4.9), computed on the GPU.  Meant for moderate sizes.
+ */
+
+/*
+ * zl_column_svd -- the per-column singular value decomposition of Eq. svdOfAm
+ * (Sec. 3.9), A_m = E_m Lambda_m F_m^T, for every grid column m of the plan's
+ * ensemble copy (its storage precision), in FP64, by one-sided Jacobi
+ * rotations (a warp per column).  g = min(nw, K) <= 64.
+ *
+ *   E    device, double [nh][nw][g]: E_m, orthonormal columns
+ *   lam  device, double [nh][g]: the singular values, descending
+ *   F    device, double [nh][K][g]: F_m, orthonormal columns
+ *
+ * Sign convention: in each singular triplet the entry of largest magnitude of
+ * F_m's column is positive.  Stream-ordered; allocates nothing.  Errors:
+ * ZL_ERR_ARG (null pointers, invalid plan), ZL_ERR_RANK (a rank-deficient
+ * plan), ZL_ERR_SHAPE (g > 64), ZL_ERR_CUDA.
+ */
+zl_status zl_column_svd(zl_plan plan, double* E, double* lam, double* F, void* stream);
+
+/*
+ * zl_xi_indicators -- the matrix-form accuracy indicators of Sec. 4.8:
+ * Xi = I - M M^T for M = Zh^- Zh (so that Zh^- Ph Zh^-^T = M M^T with
+ * Ph = Zh Zh^T, Eq. MatrixDifferenceSwiftAlgorithm), reduced on the device to
+ *   out[0] = sum_ij Xi_ij^2   (the paper's RMSE_Xi is its square root: a
+ *                              Frobenius norm, no mean)
+ *   out[1] = max_ij |Xi_ij|    (MAX_Xi)
+ *   M    device, double [n][n] row-major (column j = Zh^- Zh e_j, built with
+ *        the plan's own applies); n = K L.
+ *   out  device, double[2]; overwritten (cleared on `stream` first).
+ * FP64 CUDA-core tiles, O(n^3) work.  Errors: ZL_ERR_ARG, ZL_ERR_SHAPE
+ * (n > 2^20), ZL_ERR_CUDA.
+ */
+zl_status zl_xi_indicators(const double* M, int n, double* out, void* stream);
+
+/*
+ * zl_delta -- the vector-form indicator of Sec. 4.9 (Eq. vectorDifferencedelta,
+ * RMSEdelta): d = x~ - back and ||d_r||_2 per right-hand side, where the caller
+ * formed back = Zh^- (Zh x~) with zl_apply_sqrt and zl_apply_left_inverse.
+ *   xt, back  device, [R][K][L] in the plan's element type, read only
+ *   d         device, [R][K][L], written (may alias xt or back)
+ *   norms     device, double[R], written
+ * Errors: ZL_ERR_ARG, ZL_ERR_CUDA.
+ */
+zl_status zl_delta(zl_plan plan, const void* xt, const void* back, void* d, double* norms, int R, void* stream);
 
 /* zl_destroy -- free a plan and everything it owns (NULL is a no-op).  The
  * caller must make sure no queued apply still uses it. */

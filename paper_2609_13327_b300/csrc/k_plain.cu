@@ -35,12 +35,14 @@ constexpr size_t kRowSmemBudget = 72 * 1024;
 template <typename T, int RC>
 __global__ void __launch_bounds__(kThreads)
 fwd_column_xpass(const T* __restrict__ x, const T* __restrict__ M, const T* __restrict__ bx, T* __restrict__ t1,
-                 int R, int nw, int K, int nx, int ny, int Px) {
+                 int R, int nw, int K, int nx, int ny, int Px, int y0, long long nh_m) {
     extern __shared__ unsigned char smem_raw[];
     T* W = reinterpret_cast<T*>(smem_raw);   // [KC][RC][ldw]
     const int ldw = nx + 1;
     // member chunk fastest, then rhs chunk, then grid row: the CTAs that share a
-    // row's x and M tiles run back to back and find them in L2
+    // row's x and M tiles run back to back and find them in L2.  x holds the ny rows
+    // y0 .. y0 + ny - 1 of the grid (all of it when y0 = 0 and ny is the grid's), M the
+    // whole grid (nh_m columns); t1 rows are relative to y0.
     const int k0 = blockIdx.x * KC;
     const int r0 = blockIdx.y * RC;
     const int y = blockIdx.z;
@@ -48,6 +50,7 @@ fwd_column_xpass(const T* __restrict__ x, const T* __restrict__ M, const T* __re
 
     for (int xc = threadIdx.x; xc < nx; xc += blockDim.x) {
         const long long m = (long long)y * nx + xc;
+        const long long mm = (long long)(y0 + y) * nx + xc;
         T acc[RC][KC];
 #pragma unroll
         for (int r = 0; r < RC; ++r)
@@ -60,7 +63,7 @@ fwd_column_xpass(const T* __restrict__ x, const T* __restrict__ M, const T* __re
                 xv[r] = (r0 + r < R) ? x[((long long)(r0 + r) * nw + l) * nh + m] : T(0);
 #pragma unroll
             for (int k = 0; k < KC; ++k) {
-                const T pv = (k0 + k < K) ? M[((long long)(k0 + k) * nw + l) * nh + m] : T(0);
+                const T pv = (k0 + k < K) ? M[((long long)(k0 + k) * nw + l) * nh_m + mm] : T(0);
 #pragma unroll
                 for (int r = 0; r < RC; ++r) acc[r][k] = fma(pv, xv[r], acc[r][k]);
             }
@@ -130,7 +133,7 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads)
 fwd_ypass(const T* __restrict__ t1, const T* __restrict__ by, const int* __restrict__ m_py,
           const int* __restrict__ m_jx, const T* __restrict__ scale, T* __restrict__ out,
-          int R, int K, int ny, int Px, int ldp, int L, int ychunk) {
+          int R, int K, int ny, int Px, int ldp, int L, int ychunk, int by_ld, int y_off) {
     extern __shared__ unsigned char smem_raw[];
     T* acc = reinterpret_cast<T*>(smem_raw);   // [L]
     T* tile = acc + L;                         // [Px][ychunk + 1]: odd stride, conflict-free rows
@@ -148,7 +151,7 @@ fwd_ypass(const T* __restrict__ t1, const T* __restrict__ by, const int* __restr
         }
         __syncthreads();
         for (int j = threadIdx.x; j < L; j += blockDim.x) {
-            const T* b = by + (size_t)m_py[j] * ny + y0;
+            const T* b = by + (size_t)m_py[j] * by_ld + y_off + y0;
             const T* t = tile + (size_t)m_jx[j] * ldt;
             T s0 = 0, s1 = 0;
             int yy = 0;
@@ -162,7 +165,7 @@ fwd_ypass(const T* __restrict__ t1, const T* __restrict__ by, const int* __restr
     }
     __syncthreads();
     T* o = out + ((long long)r * K + k) * L;
-    for (int j = threadIdx.x; j < L; j += blockDim.x) o[j] = acc[j] * scale[j];
+    for (int j = threadIdx.x; j < L; j += blockDim.x) o[j] = scale ? acc[j] * scale[j] : acc[j];
 }
 
 // ---------------------------------------------------------------------------
@@ -242,27 +245,26 @@ inline int pick_rc(const zl_plan_s& p, int R, size_t row) {
     return 1;
 }
 
-template <typename T>
-cudaError_t launch_fwd(const zl_plan_s& p, const T* x, const T* M, const T* bx, T* t1, int R, cudaStream_t s);
-
 template <typename T, int RC>
-cudaError_t launch_fwd_rc(const zl_plan_s& p, const T* x, const T* M, const T* bx, T* t1, int R, cudaStream_t s) {
-    const int nx = p.d.nx, ny = p.d.ny, K = p.d.K;
+cudaError_t launch_fwd_rc(const zl_plan_s& p, const T* x, const T* M, const T* bx, T* t1, int R, cudaStream_t s,
+                          Rows rows) {
+    const int nx = p.d.nx, ny = rows.ny, K = p.d.K;
     const size_t smem = (size_t)KC * RC * (nx + 1) * sizeof(T);
     cudaError_t e = cudaFuncSetAttribute(fwd_column_xpass<T, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((K + KC - 1) / KC, (R + RC - 1) / RC, ny);
-    fwd_column_xpass<T, RC><<<grid, kThreads, smem, s>>>(x, M, bx, t1, R, p.d.nw, K, nx, ny, p.Px);
+    fwd_column_xpass<T, RC><<<grid, kThreads, smem, s>>>(x, M, bx, t1, R, p.d.nw, K, nx, ny, p.Px, rows.y0, p.nh);
     return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_fwd(const zl_plan_s& p, const T* x, const T* M, const T* bx, T* t1, int R, cudaStream_t s) {
+cudaError_t launch_fwd(const zl_plan_s& p, const T* x, const T* M, const T* bx, T* t1, int R, cudaStream_t s,
+                       Rows rows) {
     switch (pick_rc(p, R, (size_t)KC * (p.d.nx + 1) * sizeof(T))) {
-        case 8: return launch_fwd_rc<T, 8>(p, x, M, bx, t1, R, s);
-        case 4: return launch_fwd_rc<T, 4>(p, x, M, bx, t1, R, s);
-        case 2: return launch_fwd_rc<T, 2>(p, x, M, bx, t1, R, s);
-        default: return launch_fwd_rc<T, 1>(p, x, M, bx, t1, R, s);
+        case 8: return launch_fwd_rc<T, 8>(p, x, M, bx, t1, R, s, rows);
+        case 4: return launch_fwd_rc<T, 4>(p, x, M, bx, t1, R, s, rows);
+        case 2: return launch_fwd_rc<T, 2>(p, x, M, bx, t1, R, s, rows);
+        default: return launch_fwd_rc<T, 1>(p, x, M, bx, t1, R, s, rows);
     }
 }
 
@@ -333,7 +335,10 @@ fwd_ypass_gemm(const T* __restrict__ t1, const T* __restrict__ byk, const int* _
         const long long pr = (long long)blockIdx.x * ppc + pp;
         if (pr >= npairs) break;
         const T* so = sout + (size_t)pp * PYT * Px;
-        for (int j = tid; j < L; j += blockDim.x) out[pr * L + j] = so[m_ipy[j] * Px + m_jx[j]] * scale[j];
+        for (int j = tid; j < L; j += blockDim.x) {
+            const T v = so[m_ipy[j] * Px + m_jx[j]];
+            out[pr * L + j] = scale ? v * scale[j] : v;
+        }
     }
 }
 
@@ -487,14 +492,17 @@ fwd_ypass_async(const float* __restrict__ t1, const float* __restrict__ byk, con
     for (int pp = 0; pp < npl; ++pp) {
         const float* so = sout + (size_t)pp * spitch;
         float* o = out + (pair0 + pp) * L;
-        for (int j = tid; j < L; j += blockDim.x) o[j] = so[m_ipy[j] * Px + m_jx[j]] * scale[j];
+        for (int j = tid; j < L; j += blockDim.x) {
+            const float v = so[m_ipy[j] * Px + m_jx[j]];
+            o[j] = scale ? v * scale[j] : v;
+        }
     }
 }
 
 template <int PYT>
 cudaError_t launch_ypass_async(const zl_plan_s& p, const float* t1, int ldp, const float* byk, const int* m_ipy,
                                const int* m_jx, const int* yneed, const float* scale, float* out, int R,
-                               cudaStream_t s) {
+                               cudaStream_t s, Rows rows) {
     const int npairs = R * p.d.K;
     const int ppc = kThreads / (ldp / 2);                       // pairs per CTA: ldp / 2 threads each
     const size_t stream = (size_t)2 * kYAsync * ppc * ldp + 2 * kYAsync * PYT,
@@ -504,15 +512,15 @@ cudaError_t launch_ypass_async(const zl_plan_s& p, const float* t1, int ldp, con
     if (e != cudaSuccess) return e;
     const int grid = (npairs + ppc - 1) / ppc;
     p.timer.begin(ZL_STAGE_FWD_YPASS, s);
-    fwd_ypass_async<PYT><<<grid, kThreads, smem, s>>>(t1, byk, m_ipy, m_jx, yneed, scale, out, npairs, ppc, p.d.ny,
-                                                      p.Px, ldp, p.L, p.pys);
+    fwd_ypass_async<PYT><<<grid, kThreads, smem, s>>>(t1, byk + (size_t)rows.y0 * p.pys, m_ipy, m_jx, yneed, scale,
+                                                      out, npairs, ppc, rows.ny, p.Px, ldp, p.L, p.pys);
     p.timer.end(s);
     return cudaGetLastError();
 }
 
 template <typename T, int PYT>
 cudaError_t launch_ypass_gemm(const zl_plan_s& p, const T* t1, int ldp, const T* byk, const int* m_ipy,
-                              const int* m_jx, const T* scale, T* out, int R, cudaStream_t s) {
+                              const int* m_jx, const T* scale, T* out, int R, cudaStream_t s, Rows rows) {
     const int npairs = R * p.d.K;
     const int ppc = kThreads / p.Px;
     const size_t smem = ((size_t)kYChunk * PYT + (size_t)ppc * PYT * p.Px) * sizeof(T);
@@ -520,24 +528,24 @@ cudaError_t launch_ypass_gemm(const zl_plan_s& p, const T* t1, int ldp, const T*
     if (e != cudaSuccess) return e;
     const int grid = (npairs + ppc - 1) / ppc;
     p.timer.begin(ZL_STAGE_FWD_YPASS, s);
-    fwd_ypass_gemm<T, PYT><<<grid, kThreads, smem, s>>>(t1, byk, m_ipy, m_jx, scale, out, npairs, ppc, p.d.ny, p.Px,
-                                                         ldp, p.L, p.pys);
+    fwd_ypass_gemm<T, PYT><<<grid, kThreads, smem, s>>>(t1, byk + (size_t)rows.y0 * p.pys, m_ipy, m_jx, scale, out,
+                                                         npairs, ppc, rows.ny, p.Px, ldp, p.L, p.pys);
     p.timer.end(s);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_ypass(const zl_plan_s& p, const T* t1, int ldp, const T* by, const int* m_py, const int* m_jx,
-                         const T* scale, T* out, int R, cudaStream_t s, const Tables<T>* tb = nullptr) {
-    const int ny = p.d.ny, K = p.d.K;
+                         const T* scale, T* out, int R, cudaStream_t s, const Tables<T>* tb, Rows rows) {
+    const int ny = rows.ny, K = p.d.K;
     if (tb != nullptr && p.Px <= kThreads) {
-        if (p.Py <= 8) return launch_ypass_gemm<T, 8>(p, t1, ldp, tb->byk, tb->m_ipy, m_jx, scale, out, R, s);
-        if (p.Py <= 16) return launch_ypass_gemm<T, 16>(p, t1, ldp, tb->byk, tb->m_ipy, m_jx, scale, out, R, s);
-        if (p.Py <= 24) return launch_ypass_gemm<T, 24>(p, t1, ldp, tb->byk, tb->m_ipy, m_jx, scale, out, R, s);
-        if (p.Py <= 32) return launch_ypass_gemm<T, 32>(p, t1, ldp, tb->byk, tb->m_ipy, m_jx, scale, out, R, s);
-        if (p.Py <= 40) return launch_ypass_gemm<T, 40>(p, t1, ldp, tb->byk, tb->m_ipy, m_jx, scale, out, R, s);
-        if (p.Py <= 48) return launch_ypass_gemm<T, 48>(p, t1, ldp, tb->byk, tb->m_ipy, m_jx, scale, out, R, s);
-        if (p.Py <= 64) return launch_ypass_gemm<T, 64>(p, t1, ldp, tb->byk, tb->m_ipy, m_jx, scale, out, R, s);
+        if (p.Py <= 8) return launch_ypass_gemm<T, 8>(p, t1, ldp, tb->byk, tb->m_ipy, m_jx, scale, out, R, s, rows);
+        if (p.Py <= 16) return launch_ypass_gemm<T, 16>(p, t1, ldp, tb->byk, tb->m_ipy, m_jx, scale, out, R, s, rows);
+        if (p.Py <= 24) return launch_ypass_gemm<T, 24>(p, t1, ldp, tb->byk, tb->m_ipy, m_jx, scale, out, R, s, rows);
+        if (p.Py <= 32) return launch_ypass_gemm<T, 32>(p, t1, ldp, tb->byk, tb->m_ipy, m_jx, scale, out, R, s, rows);
+        if (p.Py <= 40) return launch_ypass_gemm<T, 40>(p, t1, ldp, tb->byk, tb->m_ipy, m_jx, scale, out, R, s, rows);
+        if (p.Py <= 48) return launch_ypass_gemm<T, 48>(p, t1, ldp, tb->byk, tb->m_ipy, m_jx, scale, out, R, s, rows);
+        if (p.Py <= 64) return launch_ypass_gemm<T, 64>(p, t1, ldp, tb->byk, tb->m_ipy, m_jx, scale, out, R, s, rows);
     }
     int ychunk = ny;
     while ((size_t)(p.L + p.Px * (ychunk + 1)) * sizeof(T) > 96 * 1024 && ychunk > 1) ychunk = (ychunk + 1) / 2;
@@ -545,7 +553,8 @@ cudaError_t launch_ypass(const zl_plan_s& p, const T* t1, int ldp, const T* by, 
     cudaError_t e = cudaFuncSetAttribute(fwd_ypass<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     p.timer.begin(ZL_STAGE_FWD_YPASS, s);
-    fwd_ypass<T><<<dim3(K, R), kThreads, smem, s>>>(t1, by, m_py, m_jx, scale, out, R, K, ny, p.Px, ldp, p.L, ychunk);
+    fwd_ypass<T><<<dim3(K, R), kThreads, smem, s>>>(t1, by, m_py, m_jx, scale, out, R, K, ny, p.Px, ldp, p.L, ychunk,
+                                                    p.d.ny, rows.y0);
     p.timer.end(s);
     return cudaGetLastError();
 }
@@ -553,31 +562,36 @@ cudaError_t launch_ypass(const zl_plan_s& p, const T* t1, int ldp, const T* by, 
 }  // namespace
 
 cudaError_t forward_ypass_f32(const zl_plan_s& p, const float* t1, int ldp, const float* scale, float* out, int R,
-                              cudaStream_t s) {
+                              cudaStream_t s, Rows rows) {
     // 16-byte rows and a kept y-basis that fits the register tile: the streaming form
     if (ldp % 4 == 0 && ldp / 2 <= kThreads && p.pys % 4 == 0 &&
         (size_t)(kThreads / (ldp / 2)) * ((size_t)ldp * 2 * kYAsync + (size_t)48 * p.Px) * 4 <= 200 * 1024) {
         const Tables<float>& t = p.tf;
-        if (p.Py <= 16) return launch_ypass_async<16>(p, t1, ldp, t.byk, t.m_ipy, t.m_jx, t.yneed, scale, out, R, s);
-        if (p.Py <= 24) return launch_ypass_async<24>(p, t1, ldp, t.byk, t.m_ipy, t.m_jx, t.yneed, scale, out, R, s);
-        if (p.Py <= 32) return launch_ypass_async<32>(p, t1, ldp, t.byk, t.m_ipy, t.m_jx, t.yneed, scale, out, R, s);
-        if (p.Py <= 40) return launch_ypass_async<40>(p, t1, ldp, t.byk, t.m_ipy, t.m_jx, t.yneed, scale, out, R, s);
-        if (p.Py <= 48) return launch_ypass_async<48>(p, t1, ldp, t.byk, t.m_ipy, t.m_jx, t.yneed, scale, out, R, s);
+        if (p.Py <= 16) return launch_ypass_async<16>(p, t1, ldp, t.byk, t.m_ipy, t.m_jx, t.yneed, scale, out, R, s,
+                                                          rows);
+        if (p.Py <= 24) return launch_ypass_async<24>(p, t1, ldp, t.byk, t.m_ipy, t.m_jx, t.yneed, scale, out, R, s,
+                                                          rows);
+        if (p.Py <= 32) return launch_ypass_async<32>(p, t1, ldp, t.byk, t.m_ipy, t.m_jx, t.yneed, scale, out, R, s,
+                                                          rows);
+        if (p.Py <= 40) return launch_ypass_async<40>(p, t1, ldp, t.byk, t.m_ipy, t.m_jx, t.yneed, scale, out, R, s,
+                                                          rows);
+        if (p.Py <= 48) return launch_ypass_async<48>(p, t1, ldp, t.byk, t.m_ipy, t.m_jx, t.yneed, scale, out, R, s,
+                                                          rows);
     }
-    return launch_ypass<float>(p, t1, ldp, p.tf.by, p.tf.m_py, p.tf.m_jx, scale, out, R, s, &p.tf);
+    return launch_ypass<float>(p, t1, ldp, p.tf.by, p.tf.m_py, p.tf.m_jx, scale, out, R, s, &p.tf, rows);
 }
 
 template <typename T>
 cudaError_t forward_plain(const zl_plan_s& p, const Tables<T>& t, const T* M, const T* scale, const T* x, T* out,
-                          int R, cudaStream_t s) {
+                          int R, cudaStream_t s, Rows rows) {
     T* t1 = reinterpret_cast<T*>(p.t1);
     cudaError_t e;
     p.timer.begin(ZL_STAGE_FWD_COLUMN, s);
-    e = launch_fwd<T>(p, x, M, t.bx, t1, R, s);
+    e = launch_fwd<T>(p, x, M, t.bx, t1, R, s, rows);
     p.timer.end(s);
     if (e != cudaSuccess) return e;
 
-    return launch_ypass<T>(p, t1, p.Px, t.by, t.m_py, t.m_jx, scale, out, R, s, &t);
+    return launch_ypass<T>(p, t1, p.Px, t.by, t.m_py, t.m_jx, scale, out, R, s, &t, rows);
 }
 
 template <typename T>
@@ -609,9 +623,10 @@ cudaError_t inverse_plain(const zl_plan_s& p, const Tables<T>& t, const T* M, co
 template <typename T>
 cudaError_t forward_plain_on(const zl_plan_s& p, const Tables<T>& t, const T* M, const T* scale, const T* x, T* out,
                              int R, cudaStream_t s, T* t1) {
-    cudaError_t e = launch_fwd<T>(p, x, M, t.bx, t1, R, s);
+    const Rows rows{0, p.d.ny};
+    cudaError_t e = launch_fwd<T>(p, x, M, t.bx, t1, R, s, rows);
     if (e != cudaSuccess) return e;
-    return launch_ypass<T>(p, t1, p.Px, t.by, t.m_py, t.m_jx, scale, out, R, s, &t);
+    return launch_ypass<T>(p, t1, p.Px, t.by, t.m_py, t.m_jx, scale, out, R, s, &t, rows);
 }
 
 template <typename T>
@@ -638,9 +653,9 @@ template cudaError_t forward_plain_on<float>(const zl_plan_s&, const Tables<floa
                                              const float*, float*, int, cudaStream_t, float*);
 
 template cudaError_t forward_plain<double>(const zl_plan_s&, const Tables<double>&, const double*, const double*,
-                                           const double*, double*, int, cudaStream_t);
+                                           const double*, double*, int, cudaStream_t, Rows);
 template cudaError_t forward_plain<float>(const zl_plan_s&, const Tables<float>&, const float*, const float*,
-                                          const float*, float*, int, cudaStream_t);
+                                          const float*, float*, int, cudaStream_t, Rows);
 template cudaError_t inverse_plain<double>(const zl_plan_s&, const Tables<double>&, const double*, const double*,
                                            const double*, double*, int, cudaStream_t);
 template cudaError_t inverse_plain<float>(const zl_plan_s&, const Tables<float>&, const float*, const float*,

@@ -211,7 +211,7 @@ template <int NWP>
 __global__ void __launch_bounds__(kThreadsTc, 1)
 fwd_column_tc_kernel(const __grid_constant__ CUtensorMap tmap_x, const __half* __restrict__ pimg,
                      const uint8_t* __restrict__ bximg, float* __restrict__ t1, int* __restrict__ err,
-                     int R, int K, int nx, int ny, int pxp, int starve) {
+                     int R, int K, int nx, int ny, int pxp, int starve, int y0) {
     constexpr int nwp = NWP;
     extern __shared__ __align__(1024) uint8_t smem[];
     constexpr SmemPlan sp = smem_plan(NWP);
@@ -288,14 +288,14 @@ fwd_column_tc_kernel(const __grid_constant__ CUtensorMap tmap_x, const __half* _
                     ++bc;
                 }
                 mbar_arrive_expect_tx(&bars[B_PFULL + ps], PSLOT);
-                const size_t col = (size_t)y * nx + (size_t)(gi % G) * GC + (n & 1u) * HG;
+                const size_t col = (size_t)(y + y0) * nx + (size_t)(gi % G) * GC + (n & 1u) * HG;
                 bulk_g2s(spring + ps * PSLOT, pimg + col * 128u * nwp, PSLOT, &bars[B_PFULL + ps]);
                 ++pc;
                 // warm L2 with the eight images of the group this CTA reaches two groups later
                 const uint32_t ga = gi + kL2Ahead;
                 if ((n & 1u) == 0 && ga < total_groups) {
                     const int ua = (int)blockIdx.x + (int)(ga / G) * (int)gridDim.x;
-                    const size_t cola = (size_t)(ua / n_rc) * nx + (size_t)(ga % G) * GC;
+                    const size_t cola = (size_t)(ua / n_rc + y0) * nx + (size_t)(ga % G) * GC;
                     prefetch_l2(pimg + cola * 128u * nwp, GC * PBYTES);
                 }
             }
@@ -697,32 +697,35 @@ cudaError_t tc_read_error(const zl_plan_s& p, int* code) {
     return cudaMemcpy(code, p.tc->d_err, sizeof(int), cudaMemcpyDeviceToHost);
 }
 
-cudaError_t forward_tc(const zl_plan_s& p, const float* x, float* out, int R, cudaStream_t s) {
+cudaError_t forward_tc(const zl_plan_s& p, const float* x, float* out, int R, cudaStream_t s, Rows rows,
+                       const float* scale) {
     const TcOperands& t = *p.tc;
     CUtensorMap tmap;
-    const cuuint64_t gdim[3] = {(cuuint64_t)p.nh, (cuuint64_t)p.d.nw, (cuuint64_t)R};
-    const cuuint64_t gstride[2] = {(cuuint64_t)p.nh * sizeof(float), (cuuint64_t)p.nh * p.d.nw * sizeof(float)};
+    // x holds the grid rows rows.y0 .. rows.y0 + rows.ny - 1 (the whole grid by default)
+    const cuuint64_t nhx = (cuuint64_t)rows.ny * p.d.nx;
+    const cuuint64_t gdim[3] = {nhx, (cuuint64_t)p.d.nw, (cuuint64_t)R};
+    const cuuint64_t gstride[2] = {nhx * sizeof(float), nhx * p.d.nw * sizeof(float)};
     const cuuint32_t box[3] = {(cuuint32_t)GC, (cuuint32_t)t.nwp, (cuuint32_t)RC};
     const cuuint32_t estride[3] = {1, 1, 1};
     const CUresult cr = encode_fn()(&tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(x), gdim, gstride, box,
                                     estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (cr != CUDA_SUCCESS) return cudaErrorInvalidValue;
-    const int units = p.d.ny * ((R + RC - 1) / RC);
+    const int units = rows.ny * ((R + RC - 1) / RC);
     const int grid = units < t.num_sms ? units : t.num_sms;
     p.timer.begin(ZL_STAGE_FWD_COLUMN, s);
     if (t.nwp == 16)
         fwd_column_tc_kernel<16><<<grid, kThreadsTc, t.smem, s>>>(tmap, t.pimg, t.bximg, reinterpret_cast<float*>(p.t1),
-                                                                  t.d_err, R, p.d.K, p.d.nx, p.d.ny, t.pxp,
-                                                                  p.test_wait_timeout);
+                                                                  t.d_err, R, p.d.K, p.d.nx, rows.ny, t.pxp,
+                                                                  p.test_wait_timeout, rows.y0);
     else
         fwd_column_tc_kernel<32><<<grid, kThreadsTc, t.smem, s>>>(tmap, t.pimg, t.bximg, reinterpret_cast<float*>(p.t1),
-                                                                  t.d_err, R, p.d.K, p.d.nx, p.d.ny, t.pxp,
-                                                                  p.test_wait_timeout);
+                                                                  t.d_err, R, p.d.K, p.d.nx, rows.ny, t.pxp,
+                                                                  p.test_wait_timeout, rows.y0);
     p.timer.end(s);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    return forward_ypass_f32(p, reinterpret_cast<const float*>(p.t1), t.pxp, p.tf.inv_sqrt_lam, out, R, s);
+    return forward_ypass_f32(p, reinterpret_cast<const float*>(p.t1), t.pxp, scale, out, R, s, rows);
 }
 
 }  // namespace zl

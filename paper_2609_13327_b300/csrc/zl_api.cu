@@ -197,17 +197,17 @@ zl_status run(zl_plan p, Op op, const void* in, void* out, int R, void* stream) 
             double* o = (double*)out + (long long)r0 * out_len;
             const double* M = (const double*)((op == Op::LeftInverse || op == Op::Adjoint) ? p->P : p->Zc);
             const double* sc = (op == Op::LeftInverse || op == Op::Adjoint) ? p->td.inv_sqrt_lam : p->td.sqrt_lam;
-            e = fwd ? zl::forward_plain<double>(*p, p->td, M, sc, x, o, rc, s)
+            e = fwd ? zl::forward_plain<double>(*p, p->td, M, sc, x, o, rc, s, zl::Rows{0, p->d.ny})
                     : zl::inverse_plain<double>(*p, p->td, M, sc, x, o, rc, s);
         } else {
             const float* x = (const float*)in + (long long)r0 * in_len;
             float* o = (float*)out + (long long)r0 * out_len;
             if (op == Op::LeftInverse && p->d.prec == ZL_MIXED && p->tc != nullptr && !p->force_plain) {
-                e = zl::forward_tc(*p, x, o, rc, s);
+                e = zl::forward_tc(*p, x, o, rc, s, zl::Rows{0, p->d.ny}, p->tf.inv_sqrt_lam);
             } else {
                 const float* M = (const float*)((op == Op::LeftInverse || op == Op::Adjoint) ? p->P : p->Zc);
                 const float* sc = (op == Op::LeftInverse || op == Op::Adjoint) ? p->tf.inv_sqrt_lam : p->tf.sqrt_lam;
-                e = fwd ? zl::forward_plain<float>(*p, p->tf, M, sc, x, o, rc, s)
+                e = fwd ? zl::forward_plain<float>(*p, p->tf, M, sc, x, o, rc, s, zl::Rows{0, p->d.ny})
                         : zl::inverse_plain<float>(*p, p->tf, M, sc, x, o, rc, s);
             }
         }
@@ -545,6 +545,69 @@ zl_status zl_apply_left_inverse_host(zl_plan p, const void* x, void* xt, int R, 
     if (e_in != cudaSuccess) return cuda_status(e_in);
     if (e_s != cudaSuccess) return cuda_status(e_s);
     return cuda_status(e_out);
+}
+
+zl_status zl_apply_left_inverse_rows(zl_plan p, int y0, int y1, const void* x, void* partial, int R, void* stream) {
+    if (!valid_plan(p) || R < 0 || (R > 0 && (x == nullptr || partial == nullptr))) return ZL_ERR_ARG;
+    if (y0 < 0 || y1 <= y0 || y1 > p->d.ny) return ZL_ERR_SHAPE;
+    if (p->bad_column >= 0) return ZL_ERR_RANK;
+    if (R == 0) return ZL_OK;
+    if (x == partial) return ZL_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const zl::Rows rows{y0, y1 - y0};
+    const long long in_len = (long long)p->d.nw * rows.ny * p->d.nx, out_len = (long long)p->d.K * p->L;
+    for (int r0 = 0; r0 < R; r0 += p->d.max_rhs) {
+        const int rc = std::min(p->d.max_rhs, R - r0);
+        cudaError_t e;
+        if (p->d.prec == ZL_FP64) {
+            e = zl::forward_plain<double>(*p, p->td, (const double*)p->P, nullptr, (const double*)x + r0 * in_len,
+                                          (double*)partial + r0 * out_len, rc, s, rows);
+        } else if (p->d.prec == ZL_MIXED && p->tc != nullptr && !p->force_plain) {
+            e = zl::forward_tc(*p, (const float*)x + r0 * in_len, (float*)partial + r0 * out_len, rc, s, rows, nullptr);
+        } else {
+            e = zl::forward_plain<float>(*p, p->tf, (const float*)p->P, nullptr, (const float*)x + r0 * in_len,
+                                         (float*)partial + r0 * out_len, rc, s, rows);
+        }
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    return ZL_OK;
+}
+
+zl_status zl_scale_modes(zl_plan p, const void* partial, void* xt, int R, void* stream) {
+    if (!valid_plan(p) || R < 0 || (R > 0 && (partial == nullptr || xt == nullptr))) return ZL_ERR_ARG;
+    if (p->bad_column >= 0) return ZL_ERR_RANK;
+    if (R == 0) return ZL_OK;
+    const cudaError_t e = p->d.prec == ZL_FP64
+        ? zl::launch_scale_modes<double>((const double*)partial, p->td.inv_sqrt_lam, (double*)xt,
+                                         (long long)R * p->d.K, p->L, (cudaStream_t)stream)
+        : zl::launch_scale_modes<float>((const float*)partial, p->tf.inv_sqrt_lam, (float*)xt,
+                                        (long long)R * p->d.K, p->L, (cudaStream_t)stream);
+    return cuda_status(e);
+}
+
+zl_status zl_column_svd(zl_plan p, double* E, double* lam, double* F, void* stream) {
+    if (!valid_plan(p) || E == nullptr || lam == nullptr || F == nullptr) return ZL_ERR_ARG;
+    if (p->bad_column >= 0) return ZL_ERR_RANK;
+    if (p->g > 64 || zl::column_svd_smem_per_warp(p->d.nw, p->d.K) > 200 * 1024) return ZL_ERR_SHAPE;
+    return cuda_status(zl::launch_column_svd(*p, E, lam, F, (cudaStream_t)stream));
+}
+
+zl_status zl_xi_indicators(const double* M, int n, double* out, void* stream) {
+    if (M == nullptr || out == nullptr || n < 1) return ZL_ERR_ARG;
+    if (n > (1 << 20)) return ZL_ERR_SHAPE;
+    return cuda_status(zl::launch_xi(M, n, out, (cudaStream_t)stream));
+}
+
+zl_status zl_delta(zl_plan p, const void* xt, const void* back, void* d, double* norms, int R, void* stream) {
+    if (!valid_plan(p) || R < 0 || (R > 0 && (xt == nullptr || back == nullptr || d == nullptr || norms == nullptr)))
+        return ZL_ERR_ARG;
+    if (R == 0) return ZL_OK;
+    const long long len = (long long)p->d.K * p->L;
+    cudaStream_t s = (cudaStream_t)stream;
+    const cudaError_t e = p->d.prec == ZL_FP64
+        ? zl::launch_delta<double>((const double*)xt, (const double*)back, (double*)d, norms, len, R, s)
+        : zl::launch_delta<float>((const float*)xt, (const float*)back, (float*)d, norms, len, R, s);
+    return cuda_status(e);
 }
 
 zl_status zl_destroy(zl_plan p) {

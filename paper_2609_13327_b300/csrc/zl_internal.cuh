@@ -101,12 +101,20 @@ cudaError_t launch_setup_columns(const zl_desc& d, long long nh, const void* Z, 
                                  cudaStream_t s);
 size_t setup_smem_bytes(int nw, int K);
 
+// A range of grid rows: y0 .. y0 + ny - 1 (the whole grid: {0, desc.ny}).
+struct Rows {
+    int y0;
+    int ny;
+};
+
 // k_plain.cu: forward (V1-V5 shape) and inverse (V_b, then per-column product) passes
 //   forward:  out[r][k][j] = scale[j] * sum_m V_b[m][s_j] * sum_l M[k][l][m] x[r][l][m]
 //   inverse:  out[r][l][m] = sum_k M[k][l][m] * sum_j V_b[m][s_j] scale[j] c[r][k][j]
+//   forward_plain over a row range: x holds only rows y0 .. y0 + ny - 1 ([R][n_w][ny nx]); the
+//   y-sum runs over those rows only, and a null scale leaves the modes unscaled (partial sums)
 template <typename T>
 cudaError_t forward_plain(const zl_plan_s& p, const Tables<T>& t, const T* M, const T* scale, const T* x, T* out,
-                          int R, cudaStream_t s);
+                          int R, cudaStream_t s, Rows rows);
 template <typename T>
 cudaError_t forward_plain_on(const zl_plan_s& p, const Tables<T>& t, const T* M, const T* scale, const T* x, T* out,
                              int R, cudaStream_t s, T* t1);
@@ -124,14 +132,25 @@ zl_status static_scratch_prepare(const zl_plan_s& p);
 
 // y-pass of the forward transform on an FP32 intermediate with row stride ldp
 cudaError_t forward_ypass_f32(const zl_plan_s& p, const float* t1, int ldp, const float* scale, float* out, int R,
-                              cudaStream_t s);
+                              cudaStream_t s, Rows rows);
+
+// k_diag.cu: matrix-form diagnostics (per-column SVD, Xi, delta)
+size_t column_svd_smem_per_warp(int nw, int K);
+cudaError_t launch_column_svd(const zl_plan_s& p, double* E, double* Lam, double* F, cudaStream_t s);
+cudaError_t launch_xi(const double* M, int n, double* acc, cudaStream_t s);
+template <typename T>
+cudaError_t launch_scale_modes(const T* partial, const T* scale, T* xt, long long rows, int L, cudaStream_t s);
+template <typename T>
+cudaError_t launch_delta(const T* xt, const T* back, T* d, double* norms, long long len, int R, cudaStream_t s);
 
 // k_tc.cu: tensor-core left inverse (ZL_MIXED)
 bool tc_supported(const zl_plan_s& p);
 zl_status tc_prepare(zl_plan_s& p, cudaStream_t s);
 void tc_release(zl_plan_s& p);
-cudaError_t forward_tc(const zl_plan_s& p, const float* x, float* out, int R, cudaStream_t s);
+cudaError_t forward_tc(const zl_plan_s& p, const float* x, float* out, int R, cudaStream_t s, Rows rows,
+                       const float* scale);
 cudaError_t tc_read_error(const zl_plan_s& p, int* code);
 cudaError_t tc_clear_error(const zl_plan_s& p);
+
 
 }  // namespace zl

@@ -5,12 +5,15 @@
   its two indicators: the Frobenius norm (the paper's "RMSE_Xi", defined without a mean)
   and max |Xi_ij|.  M = Zh^- Zh is formed column by column on the GPU by the library's
   own kernels (the square root of every standardized unit vector, then the left
-  inverse), in chunks of the plan's max_rhs; Xi = I - M M^T is one plain GEMM.  Memory
-  and time grow as (K L)^2 and (K L)^3: meant for moderate sizes (K L of a few thousand).
-* ``delta(plan, xt)``: x~ - Zh^- Zh x~ per right-hand side and its 2-norm (Sec. 4.9).
+  inverse), in chunks of the plan's max_rhs; Xi = I - M M^T and its two reductions run
+  in libzl's FP64 kernel (``zl_xi_indicators``).  Memory and time grow as (K L)^2 and
+  (K L)^3: meant for moderate sizes (K L of a few thousand).
+* ``delta(plan, xt)``: x~ - Zh^- Zh x~ per right-hand side and its 2-norm (Sec. 4.9),
+  the difference and norms in libzl's kernel (``zl_delta``).
+* ``column_svd(plan)``: the per-column SVD A_m = E_m Lambda_m F_m^T (Eq. svdOfAm).
 
-Every operator application runs in libzl's kernels; PyTorch supplies device memory and
-the one matrix product.
+Every computation runs in libzl's kernels; PyTorch supplies device memory (and builds
+the unit vectors whose images are M's columns).
 """
 
 import torch
@@ -36,11 +39,17 @@ def zh_inverse_zh(plan, stream=None):
 def xi_indicators(plan, stream=None):
     """(||Xi||_F, max |Xi_ij|) with Xi = I - M M^T, M = Zh^- Zh."""
     M = zh_inverse_zh(plan, stream)
-    Xi = torch.eye(M.shape[0], dtype=torch.float64, device=M.device) - M @ M.T
-    return float(torch.linalg.matrix_norm(Xi)), float(Xi.abs().max())
+    sq, mx = zl.zl_xi_indicators(M, stream=stream).cpu().tolist()
+    return sq ** 0.5, mx
 
 
 def delta(plan, xt, stream=None):
     """x~ - Zh^- Zh x~ for x~ [R][K][L] and the 2-norm of each right-hand side."""
-    d = xt - zl.zl_apply_left_inverse(plan, zl.zl_apply_sqrt(plan, xt.contiguous(), stream=stream), stream=stream)
-    return d, torch.linalg.vector_norm(d.reshape(d.shape[0], -1).to(torch.float64), dim=1)
+    xt = xt.contiguous()
+    back = zl.zl_apply_left_inverse(plan, zl.zl_apply_sqrt(plan, xt, stream=stream), stream=stream)
+    return zl.zl_delta(plan, xt, back, stream=stream)
+
+
+def column_svd(plan, stream=None):
+    """(E [n_h][n_w][g], Lambda [n_h][g], F [n_h][K][g]): A_m = E_m diag(Lambda_m) F_m^T per column."""
+    return zl.zl_column_svd(plan, stream=stream)

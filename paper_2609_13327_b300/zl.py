@@ -29,7 +29,8 @@ EXPORTS = ["zl_setup", "zl_get_info", "zl_get_modes", "zl_apply_left_inverse", "
            "zl_apply_sqrt", "zl_apply_adjoint", "zl_apply_sqrt_adjoint", "zl_destroy", "zl_status_string",
            "zl_gaussian_spectrum", "zl_set_stage_timing", "zl_get_stage_times", "zl_get_runtime_info",
            "zl_apply_left_inverse_static", "zl_setup_batch", "zl_batch_get_info", "zl_apply_left_inverse_batch",
-           "zl_destroy_batch", "zl_standardize_ensemble", "zl_set_test_wait_timeout"]
+           "zl_destroy_batch", "zl_standardize_ensemble", "zl_set_test_wait_timeout", "zl_column_svd",
+           "zl_xi_indicators", "zl_delta", "zl_apply_left_inverse_rows", "zl_scale_modes"]
 STAGES = {"fwd_column": 0, "fwd_ypass": 1, "inv_ypass": 2, "inv_column": 3}
 
 
@@ -59,6 +60,11 @@ _lib.zl_setup_batch.argtypes = [_int, ctypes.POINTER(zl_desc), ctypes.POINTER(_v
 _lib.zl_batch_get_info.argtypes = [_vp, _int, ctypes.POINTER(_vp), _ip]
 _lib.zl_apply_left_inverse_batch.argtypes = [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _ip, _vp]
 _lib.zl_destroy_batch.argtypes = [_vp]
+_lib.zl_column_svd.argtypes = [_vp, _vp, _vp, _vp, _vp]
+_lib.zl_apply_left_inverse_rows.argtypes = [_vp, _int, _int, _vp, _vp, _int, _vp]
+_lib.zl_scale_modes.argtypes = [_vp, _vp, _vp, _int, _vp]
+_lib.zl_xi_indicators.argtypes = [_vp, _int, _vp, _vp]
+_lib.zl_delta.argtypes = [_vp, _vp, _vp, _vp, _vp, _int, _vp]
 for _name in EXPORTS:
     if _name != "zl_status_string":
         getattr(_lib, _name).restype = _int
@@ -244,6 +250,79 @@ def zl_apply_adjoint(plan, y, out=None, stream=None):
     """g = (Zh^-)^T y: y [R][K][L] -> g [R][n_w][n_h]."""
     return _apply(_lib.zl_apply_adjoint, plan, y, (plan.K, plan.L), (plan.nw, plan.nh), out, stream,
                   "zl_apply_adjoint")
+
+
+def zl_apply_left_inverse_rows(plan, y0, y1, x, out=None, stream=None):
+    """One slab's unscaled share of x~: x [R][n_w][(y1 - y0) nx] (the slab's rows) -> [R][K][L]."""
+    import torch
+    if not (isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == plan.dtype and x.is_contiguous()
+            and x.dim() == 3 and tuple(x.shape[1:]) == (plan.nw, (y1 - y0) * plan.nx)):
+        raise ValueError("zl_apply_left_inverse_rows: x must be a contiguous CUDA tensor [R][n_w][(y1 - y0) nx]")
+    R = x.shape[0]
+    if out is None:
+        out = torch.empty((R, plan.K, plan.L), dtype=plan.dtype, device=x.device)
+    elif not (out.is_cuda and out.dtype == plan.dtype and out.is_contiguous() and tuple(out.shape) == (R, plan.K, plan.L)):
+        raise ValueError("zl_apply_left_inverse_rows: bad output tensor")
+    _check(_lib.zl_apply_left_inverse_rows(plan.handle, int(y0), int(y1), _vp(x.data_ptr()), _vp(out.data_ptr()), R,
+                                           _stream_handle(stream)), "zl_apply_left_inverse_rows")
+    return out
+
+
+def zl_scale_modes(plan, partial, out=None, stream=None):
+    """x~ = Delta^{-1/2} partial ([R][K][L]); out may be partial itself."""
+    import torch
+    if not (isinstance(partial, torch.Tensor) and partial.is_cuda and partial.dtype == plan.dtype
+            and partial.is_contiguous() and partial.dim() == 3 and tuple(partial.shape[1:]) == (plan.K, plan.L)):
+        raise ValueError("zl_scale_modes: partial must be a contiguous CUDA tensor [R][K][L]")
+    if out is None:
+        out = torch.empty_like(partial)
+    elif not (out.is_cuda and out.dtype == plan.dtype and out.is_contiguous() and out.shape == partial.shape):
+        raise ValueError("zl_scale_modes: bad output tensor")
+    _check(_lib.zl_scale_modes(plan.handle, _vp(partial.data_ptr()), _vp(out.data_ptr()), partial.shape[0],
+                               _stream_handle(stream)), "zl_scale_modes")
+    return out
+
+
+def zl_column_svd(plan, stream=None):
+    """Per-column SVD A_m = E_m Lambda_m F_m^T (Eq. svdOfAm): (E [n_h][n_w][g], lam [n_h][g],
+    F [n_h][K][g]), float64 CUDA tensors, singular values descending."""
+    import torch
+    g = min(plan.nw, plan.K)
+    E = torch.empty((plan.nh, plan.nw, g), dtype=torch.float64, device="cuda")
+    lam = torch.empty((plan.nh, g), dtype=torch.float64, device="cuda")
+    F = torch.empty((plan.nh, plan.K, g), dtype=torch.float64, device="cuda")
+    _check(_lib.zl_column_svd(plan.handle, _vp(E.data_ptr()), _vp(lam.data_ptr()), _vp(F.data_ptr()),
+                              _stream_handle(stream)), "zl_column_svd")
+    return E, lam, F
+
+
+def zl_xi_indicators(M, stream=None):
+    """(sum of Xi_ij^2, max |Xi_ij|) of Xi = I - M M^T as a float64 CUDA tensor [2]."""
+    import torch
+    if not (isinstance(M, torch.Tensor) and M.is_cuda and M.dtype == torch.float64 and M.is_contiguous()
+            and M.dim() == 2 and M.shape[0] == M.shape[1]):
+        raise ValueError("zl_xi_indicators: M must be a contiguous square CUDA float64 tensor")
+    out = torch.empty(2, dtype=torch.float64, device=M.device)
+    _check(_lib.zl_xi_indicators(_vp(M.data_ptr()), M.shape[0], _vp(out.data_ptr()), _stream_handle(stream)),
+           "zl_xi_indicators")
+    return out
+
+
+def zl_delta(plan, xt, back, stream=None):
+    """d = x~ - back and ||d_r||_2 per right-hand side (back = Zh^- Zh x~)."""
+    import torch
+    for t in (xt, back):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == plan.dtype and t.is_contiguous()
+                and t.dim() == 3 and tuple(t.shape[1:]) == (plan.K, plan.L)):
+            raise ValueError(f"zl_delta: inputs must be contiguous CUDA {plan.dtype} tensors [R][K][L]")
+    if back.shape != xt.shape:
+        raise ValueError("zl_delta: x~ and back differ in shape")
+    R = xt.shape[0]
+    d = torch.empty_like(xt)
+    norms = torch.empty(R, dtype=torch.float64, device=xt.device)
+    _check(_lib.zl_delta(plan.handle, _vp(xt.data_ptr()), _vp(back.data_ptr()), _vp(d.data_ptr()),
+                         _vp(norms.data_ptr()), R, _stream_handle(stream)), "zl_delta")
+    return d, norms
 
 
 def zl_apply_left_inverse_host(plan, x, out=None, stream=None):

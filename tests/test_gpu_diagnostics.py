@@ -10,7 +10,7 @@ vanish to rounding."""
 import numpy as np
 import pytest
 
-from oracle import basis, dense
+from oracle import basis, compare, dense, swift
 from paper_2609_13327_b300 import synth
 
 torch = pytest.importorskip("torch")
@@ -77,3 +77,62 @@ def test_delta_matches_dense(mods):
     for r in range(len(xt)):
         ref = dense.rmse_delta(Zinv, Zh, xt[r].reshape(-1))
         assert abs(float(norms[r]) - ref) <= 1e-9 * ref
+    # the difference vector itself, element by element, against the dense brute force
+    d_ref = xt - (Zinv @ (Zh @ xt.reshape(len(xt), -1).T)).T.reshape(xt.shape)
+    compare.check(d.cpu().numpy(), d_ref, 1e-9, 2, "delta vector")
+
+
+# ---------------------------------------------------------------- per-column SVD (Eq. svdOfAm)
+
+SVD_CASES = [
+    (WIDE, "fp64"),                                                                     # n_w < K
+    (synth.Workload("svd_tall", 16, 12, 24, 16, 2.0, 0.7, 2.0, 2, "fp64", 63), "fp64"),  # n_w > K
+    (synth.WORKLOADS["c0b_paper_shape"], "fp64"),                                       # n_w = K = 64
+    (synth.Workload("svd_odd", 9, 7, 5, 11, 2.0, 0.6, 2.0, 2, "fp32", 64), "fp32"),       # odd g, FP32 copy
+]
+
+
+def sign_fixed(E, lam, F):
+    """The library's convention: the entry of largest magnitude of each F column is positive."""
+    idx = np.argmax(np.abs(F), axis=1)                                  # [n_h][g]
+    sgn = np.sign(np.take_along_axis(F, idx[:, None, :], axis=1))[:, 0, :]
+    sgn[sgn == 0] = 1.0
+    return E * sgn[:, None, :], lam, F * sgn[:, None, :]
+
+
+@pytest.mark.parametrize("w,prec", SVD_CASES, ids=[f"{w.name}-{p}" for w, p in SVD_CASES])
+def test_column_svd_matches_numpy(mods, w, prec):
+    """E_m, Lambda_m, F_m of every column against numpy.linalg.svd of the oracle's A_m (same
+    rounded ensemble), after fixing each singular pair's sign by the same rule; plus the
+    factorisation A_m = E_m Lambda_m F_m^T and the orthonormality of E_m and F_m."""
+    zl, diag = mods
+    dt = synth.storage_dtype(prec)
+    Z = synth.ensemble(w).astype(dt)
+    lam = basis.spectrum_2d(w.Nx, w.Ny, w.ell_loc)
+    plan = zl.zl_setup(torch.from_numpy(Z).cuda(), lam, tau=w.tau, prec=prec, max_rhs=4, nx=w.Nx, ny=w.Ny)
+    E, L, F = (t.cpu().numpy() for t in diag.column_svd(plan))
+    oracle = swift.Plan(Z.astype(np.float64), w.Nx, w.Ny, lam, w.tau)
+    Eo, Lo, Fo = sign_fixed(oracle.E, oracle.Lam, oracle.F)
+    smax = Lo[:, :1]
+    assert np.all(np.abs(L - Lo) <= 1e-12 * smax)
+    assert np.all(np.diff(L, axis=1) <= 0)
+    A = oracle.A                                                      # [n_h][n_w][K]
+    rec = np.einsum("mli,mi,mki->mlk", E, L, F)
+    assert np.abs(rec - A).max() <= 1e-12 * np.abs(A).max()
+    g = L.shape[1]
+    for Q in (E, F):
+        G = np.einsum("mai,maj->mij", Q, Q)
+        assert np.abs(G - np.eye(g)[None]).max() <= 1e-12
+    assert np.abs(E - Eo).max() <= 1e-8 and np.abs(F - Fo).max() <= 1e-8
+
+
+def test_xi_kernel_against_its_definition(mods):
+    """zl_xi_indicators on a random non-square-like M: sum of squares and max of I - M M^T."""
+    zl, _ = mods
+    rng = np.random.default_rng(5)
+    for n in (1, 31, 70):
+        M = rng.standard_normal((n, n)) / np.sqrt(n)
+        Xi = np.eye(n) - M @ M.T
+        out = zl.zl_xi_indicators(torch.from_numpy(M).cuda()).cpu().numpy()
+        assert abs(out[0] - np.sum(Xi ** 2)) <= 1e-12 * np.sum(Xi ** 2)
+        assert out[1] == pytest.approx(np.abs(Xi).max(), rel=1e-13)

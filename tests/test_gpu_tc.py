@@ -133,8 +133,10 @@ def test_tensor_core_square_and_tall_columns(zl, w):
     For x in the range of Zh the problem's own conditioning sets the accuracy: rounding
     x to FP32 (2^-24) already moves the FP64 oracle's Zh^- x away from x~0 by e_or,
     about eps cond(A_m) sqrt(lambda_max/lambda_min) (the bound of the delta pin).  The
-    tensor-core path represents x and A_m^+ to 2^-22 (FP16 hi/lo), so it must recover
-    x~0 within a few times e_or (8 e_or, plus the mixed tolerance)."""
+    tensor-core path represents x and A_m^+ to 2^-22 (FP16 hi/lo) and accumulates the
+    n_w-term sums of V1 in FP32 on the tensor cores, whose rounding error is amplified by
+    the same cancellation (up to about 2 sqrt(n_w) times the input rounding's effect), so
+    it must recover x~0 within 16 e_or plus the mixed tolerance."""
     Z = synth.ensemble(w).astype(np.float32)
     lam = basis.spectrum_2d(w.Nx, w.Ny, w.ell_loc)
     oracle = swift.Plan(Z.astype(np.float64), w.Nx, w.Ny, lam, w.tau)
@@ -154,4 +156,4 @@ def test_tensor_core_square_and_tall_columns(zl, w):
     e_gpu = np.linalg.norm((back - xt0).reshape(w.R, -1), axis=1)
     scale = np.linalg.norm(xt0.reshape(w.R, -1), axis=1)
     assert np.all(e_or <= 1e-3 * scale)
-    assert np.all(e_gpu <= 8 * e_or + 2 * TOL_MIXED * scale), (e_gpu / scale, e_or / scale)
+    assert np.all(e_gpu <= 16 * e_or + 2 * TOL_MIXED * scale), (e_gpu / scale, e_or / scale)
