@@ -211,7 +211,7 @@ template <int NWP>
 __global__ void __launch_bounds__(kThreadsTc, 1)
 fwd_column_tc_kernel(const __grid_constant__ CUtensorMap tmap_x, const __half* __restrict__ pimg,
                      const uint8_t* __restrict__ bximg, float* __restrict__ t1, int* __restrict__ err,
-                     int R, int K, int nx, int ny, int pxp, int starve, int y0) {
+                     int R, int K, int nx, int ny, int pxp, int starve, int y0, unsigned* __restrict__ t1max) {
     constexpr int nwp = NWP;
     extern __shared__ __align__(1024) uint8_t smem[];
     constexpr SmemPlan sp = smem_plan(NWP);
@@ -448,6 +448,17 @@ fwd_column_tc_kernel(const __grid_constant__ CUtensorMap tmap_x, const __half* _
                 tmem_regs_ready(d0);
                 tmem_regs_ready(d1);
                 tmem_regs_ready(d2);
+                if (t1max != nullptr) {   // max |t1| of the launch, for the y-pass's FP16 scaling
+                    float mx = 0.f;
+                    if (r0 + r < R && k < K)
+#pragma unroll
+                        for (int i = 0; i < 16; ++i)
+                            mx = fmaxf(mx, fmaxf(fabsf(__uint_as_float(d0[i])),
+                                                 fmaxf(fabsf(__uint_as_float(d1[i])), fabsf(__uint_as_float(d2[i])))));
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+                    if (lane == 0) atomicMax(t1max, __float_as_uint(mx));
+                }
                 if (r0 + r < R && k < K) {
                     float4* dst = reinterpret_cast<float4*>(t1 + (((size_t)y * R + r0 + r) * K + k) * pxp);
                     auto put = [&](int c, const uint32_t (&d)[16], int i) {
@@ -664,7 +675,12 @@ zl_status tc_prepare(zl_plan_s& p, cudaStream_t s) {
         e = t->nwp == 16
                 ? cudaFuncSetAttribute(fwd_column_tc_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t->smem)
                 : cudaFuncSetAttribute(fwd_column_tc_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t->smem);
+    if (e == cudaSuccess) {   // the tensor-core y-pass, where its shape fits (else the CUDA-core one)
+        const zl_status ys = ytc_prepare(p, t->pxp, s);
+        if (ys != ZL_OK && ys != ZL_ERR_UNSUPPORTED) e = ys == ZL_ERR_ALLOC ? cudaErrorMemoryAllocation : cudaErrorUnknown;
+    }
     if (e != cudaSuccess) {
+        ytc_release(p);
         cudaFree(t->pimg);
         cudaFree(t->bximg);
         cudaFree(t->d_err);
@@ -676,6 +692,7 @@ zl_status tc_prepare(zl_plan_s& p, cudaStream_t s) {
 }
 
 void tc_release(zl_plan_s& p) {
+    ytc_release(p);
     if (!p.tc) return;
     cudaFree(p.tc->pimg);
     cudaFree(p.tc->bximg);
@@ -688,13 +705,20 @@ int tc_t1_stride(const zl_plan_s& p) { return p.tc ? p.tc->pxp : p.Px; }
 
 cudaError_t tc_clear_error(const zl_plan_s& p) {
     if (!p.tc) return cudaSuccess;
-    return cudaMemset(p.tc->d_err, 0, sizeof(int));
+    const cudaError_t e = cudaMemset(p.tc->d_err, 0, sizeof(int));
+    return e != cudaSuccess ? e : ytc_clear_error(p);
 }
 
+// The column kernel's code, else the y-pass's (plus 16: codes of the tensor-core y-pass).
 cudaError_t tc_read_error(const zl_plan_s& p, int* code) {
     *code = 0;
     if (!p.tc) return cudaSuccess;
-    return cudaMemcpy(code, p.tc->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaError_t e = cudaMemcpy(code, p.tc->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess || *code != 0) return e;
+    int yc = 0;
+    e = ytc_read_error(p, &yc);
+    if (yc != 0) *code = 16 + yc;
+    return e;
 }
 
 cudaError_t forward_tc(const zl_plan_s& p, const float* x, float* out, int R, cudaStream_t s, Rows rows,
@@ -713,18 +737,26 @@ cudaError_t forward_tc(const zl_plan_s& p, const float* x, float* out, int R, cu
     if (cr != CUDA_SUCCESS) return cudaErrorInvalidValue;
     const int units = rows.ny * ((R + RC - 1) / RC);
     const int grid = units < t.num_sms ? units : t.num_sms;
+    // the tensor-core y-pass needs the whole grid (its basis image starts at row 0) and max |t1|
+    const bool ytc = p.ytc != nullptr && rows.y0 == 0 && rows.ny == p.d.ny;
+    unsigned* t1max = ytc ? ytc_max_word(p) : nullptr;
+    if (t1max != nullptr) {
+        const cudaError_t em = cudaMemsetAsync(t1max, 0, sizeof(unsigned), s);
+        if (em != cudaSuccess) return em;
+    }
     p.timer.begin(ZL_STAGE_FWD_COLUMN, s);
     if (t.nwp == 16)
         fwd_column_tc_kernel<16><<<grid, kThreadsTc, t.smem, s>>>(tmap, t.pimg, t.bximg, reinterpret_cast<float*>(p.t1),
                                                                   t.d_err, R, p.d.K, p.d.nx, rows.ny, t.pxp,
-                                                                  p.test_wait_timeout, rows.y0);
+                                                                  p.test_wait_timeout, rows.y0, t1max);
     else
         fwd_column_tc_kernel<32><<<grid, kThreadsTc, t.smem, s>>>(tmap, t.pimg, t.bximg, reinterpret_cast<float*>(p.t1),
                                                                   t.d_err, R, p.d.K, p.d.nx, rows.ny, t.pxp,
-                                                                  p.test_wait_timeout, rows.y0);
+                                                                  p.test_wait_timeout, rows.y0, t1max);
     p.timer.end(s);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    if (ytc) return forward_ypass_tc(p, reinterpret_cast<const float*>(p.t1), t.pxp, scale, out, R, s);
     return forward_ypass_f32(p, reinterpret_cast<const float*>(p.t1), t.pxp, scale, out, R, s, rows);
 }
 

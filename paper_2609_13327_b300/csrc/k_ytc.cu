@@ -1,0 +1,491 @@
+// Tensor-core y-pass of the mixed-precision left inverse: the second half of step V4
+// (Sec. 3.10), x~_k[j] = lambda_j^{-1/2} sum_y b_{p_y(j)}(y) c_k(y, p_x(j)), with
+// c = t1 the x-pass output of the column kernel, stored [ny][R K][ldp] (ldp = Px
+// rounded up to 4).
+//
+// As a GEMM: rows m = (pair, x-frequency slot) of t1, K = y, N = the kept y-frequencies.
+//   D[m][i]       = sum_y T(m, y) b_hi(i, y)      (i < PYB)
+//   D[m][PYB + i] = sum_y T(m, y) b_lo(i, y)
+// with T = T_hi + T_lo split to FP16 and the K dimension carrying both halves
+// ([T_hi | T_lo] against [b | b] per 8 rows of y), so every one of the four
+// products is accumulated in FP32 in TMEM; the epilogue adds the two N halves.
+// The basis is scaled by 16 (exactly) so that b_lo stays a normal FP16 number, and
+// T by a power of two chosen from max |t1| (recorded by the column kernel), so that
+// T_hi cannot overflow and T_lo keeps its precision; both scalings are undone
+// exactly in the epilogue.
+//
+// A unit is ppu = floor(128 / ldp) pairs (M = ppu * ldp <= 128 rows) over all y.  Warp
+// roles (320 threads): warp 0 lane 0 = producer (one 2-D tensor copy of 32 y-rows of
+// the unit's t1 block plus the basis of those rows per stage), warp 1 = TMEM
+// allocator + MMA issuer, warps 2-5 = converters (thread = row m: FP32 -> scaled FP16
+// hi/lo A operand, 8 rows of y per slot), warps 6-9 = epilogue (TMEM -> per-pair mode
+// gather -> x~, through a shared staging tile).  Accumulators are double-buffered in
+// TMEM so the drain of unit u overlaps the MMAs of unit u + 1.  All waits are bounded.
+
+#include "zl_internal.cuh"
+#include "tc_ptx.cuh"
+
+#include <cuda.h>
+#include <cuda_fp16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+namespace zl {
+
+struct YtcOperands {
+    __half* bimg = nullptr;    // per y-block of 8 rows: N rows x [chunk 0 | chunk 1] x 8 FP16, K-major core matrices
+    unsigned* t1max = nullptr; // max |t1| (float bits), written by the column kernel
+    int* d_err = nullptr;
+    int pyb = 0;               // kept y-frequencies rounded up to 8
+    int nstage_y = 0;          // stages of 32 rows of y covering ny
+    uint32_t smem = 0;
+};
+
+namespace {
+
+using namespace tc;
+
+constexpr int YC = 32;                  // rows of y per stage (one tensor copy)
+constexpr int YB = 8;                   // rows of y per MMA (one A slot)
+constexpr int S = 4;                    // stage ring depth
+constexpr int SA = 2 * (YC / YB);       // A slots: two groups of one stage's 8-row blocks
+constexpr int kThreads = 320;
+constexpr int kConvWarp0 = 2, kEpiWarp0 = 6;
+constexpr uint32_t kTmemCols = 256;     // two accumulators of up to 128 columns
+constexpr uint32_t kASlot = 4096;       // 128 rows x 32 B
+constexpr float kBasisScale = 16.0f;
+constexpr unsigned long long kWaitCycles = 4000000000ull;
+
+enum { B_FULL = 0, B_EMPTY = B_FULL + S, B_AFULL = B_EMPTY + S, B_DFULL = B_AFULL + SA,
+       B_DEMPTY = B_DFULL + 2, B_GFULL = B_DEMPTY + 2, B_GFREE, B_FIN, B_COUNT };
+
+struct Plan {
+    uint32_t stage_t, stage_b, stage, ring, aring, gather, bars, total;
+};
+
+// rows_u = ppu * ldp rows of t1 per stage row of y; nb = N = 2 * pyb
+__host__ __device__ inline Plan smem_plan(int rows_u, int nb) {
+    Plan s{};
+    s.stage_t = ((uint32_t)rows_u * YC * 4u + 1023u) & ~1023u;
+    s.stage_b = (uint32_t)(YC / YB) * (uint32_t)nb * 32u;
+    s.stage = (s.stage_t + s.stage_b + 1023u) & ~1023u;
+    uint32_t o = 0;
+    s.ring = o;
+    o += S * s.stage;
+    s.aring = o;
+    o += SA * kASlot;
+    s.gather = o;
+    o += 128u * (uint32_t)(nb / 2 + 1) * 4u;
+    o = (o + 127u) & ~127u;
+    s.bars = o;
+    o += ((B_COUNT * 8u + 8u) + 127u) & ~127u;
+    s.total = o;
+    return s;
+}
+
+__device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    for (uint32_t i = 1;; ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((i & 1023u) == 0u) {
+            if (*abort_flag) return false;
+            if ((unsigned long long)(clock64() - t0) > kWaitCycles) return false;
+        }
+    }
+}
+
+__device__ __forceinline__ bool warp_wait_bar(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+    const bool ok = wait_bar(bar, parity, abort_flag);
+    return __all_sync(0xffffffffu, ok);
+}
+
+__device__ __forceinline__ void fail(volatile int* abort_flag, int* err, int code) {
+    *abort_flag = 1;
+    atomicCAS(err, 0, code);
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const void* tmap, int c0, int c1, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(smem_u32(dst)), "l"(tmap), "r"(c0), "r"(c1), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// 16 consecutive TMEM columns of this lane -> v[0..15]
+__device__ __forceinline__ void ld16(uint32_t taddr, float* v) {
+    uint32_t r[16];
+    tmem_ld16(taddr, r);
+    tmem_ld_wait();
+    tmem_regs_ready(r);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <int NB>
+__global__ void __launch_bounds__(kThreads, 1)
+fwd_ypass_tc_kernel(const __grid_constant__ CUtensorMap tmap_t, const __half* __restrict__ bimg,
+                    const unsigned* __restrict__ t1max, const int* __restrict__ m_ipy, const int* __restrict__ m_jx,
+                    const float* __restrict__ scale, float* __restrict__ out, int* __restrict__ err, int npairs,
+                    int ldp, int ppu, int L, int nstage_y) {
+    constexpr int PYB = NB / 2;
+    extern __shared__ __align__(1024) uint8_t smem[];
+    const int rows_u = ppu * ldp;
+    const Plan sp = smem_plan(rows_u, NB);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + sp.bars);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + B_COUNT);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
+    float* gather = reinterpret_cast<float*>(smem + sp.gather);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int units = (npairs + ppu - 1) / ppu;
+    const int my_units = (int)blockIdx.x < units ? (units - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const uint32_t tbytes = (uint32_t)rows_u * YC * 4u;
+
+    if (tid == 0) {
+        for (int i = 0; i < S; ++i) {
+            mbar_init(&bars[B_FULL + i], 1);
+            mbar_init(&bars[B_EMPTY + i], 1);
+        }
+        for (int i = 0; i < SA; ++i) mbar_init(&bars[B_AFULL + i], 128);
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&bars[B_DFULL + i], 1);
+            mbar_init(&bars[B_DEMPTY + i], 128);
+        }
+        mbar_init(&bars[B_GFULL], 128);
+        mbar_init(&bars[B_GFREE], 128);
+        mbar_init(&bars[B_FIN], 1);
+        *abort_flag = 0;
+        fence_mbar_init();
+        prefetch_tmap(&tmap_t);
+    }
+    if (warp == 1) tmem_alloc(tslot, kTmemCols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = *tslot;
+
+    if (warp == 0) {
+        // ------------------------------------------------------------ producer
+        if (lane == 0) {
+            uint32_t sc = 0;
+            for (int ui = 0; ui < my_units && !*abort_flag; ++ui) {
+                const int u = (int)blockIdx.x + ui * (int)gridDim.x;
+                for (int st = 0; st < nstage_y; ++st, ++sc) {
+                    const uint32_t s = sc % S;
+                    if (sc >= S && !wait_bar(&bars[B_EMPTY + s], ((sc / S) - 1) & 1u, abort_flag)) {
+                        fail(abort_flag, err, 1);
+                        break;
+                    }
+                    uint8_t* dst = smem + sp.ring + s * sp.stage;
+                    mbar_arrive_expect_tx(&bars[B_FULL + s], tbytes + sp.stage_b);
+                    tma_load_2d(dst, &tmap_t, u * rows_u, st * YC, &bars[B_FULL + s]);
+                    bulk_g2s(dst + sp.stage_t, bimg + (size_t)st * (sp.stage_b / 2), sp.stage_b, &bars[B_FULL + s]);
+                }
+            }
+            // every issued copy lands before the CTA exits
+            for (uint32_t s = 0; s < S && s < sc; ++s) {
+                const uint32_t n = (sc - s + S - 1) / S;
+                const long long t0 = clock64();
+                while (!mbar_try_wait(&bars[B_FULL + s], (n - 1) & 1u) && (unsigned long long)(clock64() - t0) < kWaitCycles) {}
+            }
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            constexpr uint32_t idesc = idesc_f16_f32(128, NB);
+            const uint64_t dA0 = smem_desc(smem_u32(smem + sp.aring), 128u, 256u);
+            const uint64_t dB0 = smem_desc(smem_u32(smem + sp.ring + sp.stage_t), 128u, 256u);
+            bool ok = true;
+            uint32_t sc = 0;
+            for (int ui = 0; ui < my_units && ok; ++ui) {
+                const uint32_t d = (uint32_t)ui & 1u;
+                if (ui >= 2 && !wait_bar(&bars[B_DEMPTY + d], ((ui >> 1) - 1) & 1u, abort_flag)) { ok = false; break; }
+                tc_fence_after();
+                for (int st = 0; st < nstage_y && ok; ++st, ++sc) {
+                    const uint32_t s = sc % S;
+                    if (!wait_bar(&bars[B_FULL + s], (sc / S) & 1u, abort_flag)) { ok = false; break; }
+                    for (int b = 0; b < YC / YB; ++b) {
+                        // A group sc % 2 (slots a) is refilled once the commit of stage sc - 2 has arrived
+                        const uint32_t a = (sc & 1u) * (YC / YB) + (uint32_t)b;
+                        if (!wait_bar(&bars[B_AFULL + a], (sc >> 1) & 1u, abort_flag)) { ok = false; break; }
+                        tc_fence_after();
+                        const uint64_t da = dA0 + ((a * kASlot) >> 4);
+                        const uint64_t db = dB0 + ((s * sp.stage + (uint32_t)b * NB * 32u) >> 4);
+                        mma_f16(tbase + d * 128u, da, db, idesc, (st > 0 || b > 0) ? 1u : 0u);
+                    }
+                    // one commit per stage frees its T block, its basis and its A group
+                    if (ok) mma_commit(&bars[B_EMPTY + s]);
+                }
+                if (ok) mma_commit(&bars[B_DFULL + d]);
+            }
+            if (!ok) fail(abort_flag, err, 2);
+            mma_commit(&bars[B_FIN]);
+            const long long t0 = clock64();
+            while (!mbar_try_wait(&bars[B_FIN], 0) && (unsigned long long)(clock64() - t0) < kWaitCycles) {}
+        }
+    } else if (warp < kEpiWarp0) {
+        // ------------------------------------------------------------ converters: row m
+        const int m = tid - 32 * kConvWarp0;                      // 0 .. 127
+        int e2 = 0;
+        (void)frexpf(__uint_as_float(*t1max), &e2);
+        e2 = max(-100, min(100, e2));
+        const float ts = ldexpf(1.0f, 14 - e2);                    // max |T| * ts < 2^14
+        bool ok = true;
+        uint32_t sc = 0;
+        for (int ui = 0; ui < my_units && ok; ++ui) {
+            for (int st = 0; st < nstage_y && ok; ++st, ++sc) {
+                const uint32_t s = sc % S;
+                if (!warp_wait_bar(&bars[B_FULL + s], (sc / S) & 1u, abort_flag)) { ok = false; break; }
+                // A group sc % 2 was last read by the MMAs of stage sc - 2
+                if (sc >= 2) {
+                    const uint32_t sp2 = sc - 2;
+                    if (!warp_wait_bar(&bars[B_EMPTY + sp2 % S], (sp2 / S) & 1u, abort_flag)) { ok = false; break; }
+                }
+                const float* tt = reinterpret_cast<const float*>(smem + sp.ring + s * sp.stage);
+                for (int b = 0; b < YC / YB; ++b) {
+                    const uint32_t a = (sc & 1u) * (YC / YB) + (uint32_t)b;
+                    if (m < rows_u) {
+                        float v[YB];
+#pragma unroll
+                        for (int e = 0; e < YB; ++e) v[e] = tt[(b * YB + e) * rows_u + m] * ts;
+                        uint32_t hi[4], lo[4];
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const __half2 h = __floats2half2_rn(v[2 * e], v[2 * e + 1]);
+                            const float2 hf = __half22float2(h);
+                            const __half2 l = __floats2half2_rn(v[2 * e] - hf.x, v[2 * e + 1] - hf.y);
+                            hi[e] = *reinterpret_cast<const uint32_t*>(&h);
+                            lo[e] = *reinterpret_cast<const uint32_t*>(&l);
+                        }
+                        uint8_t* dst = smem + sp.aring + a * kASlot + (m >> 3) * 256u + (m & 7) * 16u;
+                        *reinterpret_cast<uint4*>(dst) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+                        *reinterpret_cast<uint4*>(dst + 128u) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+                    }
+                    fence_proxy_async_smem();
+                    mbar_arrive(&bars[B_AFULL + a]);
+                }
+            }
+        }
+        if (!ok) fail(abort_flag, err, 3);
+    } else {
+        // ------------------------------------------------------------ epilogue
+        const int q = warp & 3;                                    // TMEM lane quarter
+        const int m = 32 * q + lane;                               // accumulator row
+        const int et = tid - 32 * kEpiWarp0;                       // 0 .. 127
+        int e2 = 0;
+        (void)frexpf(__uint_as_float(*t1max), &e2);
+        e2 = max(-100, min(100, e2));
+        const float unscale = ldexpf(1.0f, e2 - 14) / kBasisScale;
+        const uint32_t lane_off = (uint32_t)(32 * q) << 16;
+        constexpr int GP = PYB + 1;                                // gather row pitch (odd)
+        bool ok = true;
+        for (int ui = 0; ui < my_units && ok; ++ui) {
+            const int u = (int)blockIdx.x + ui * (int)gridDim.x;
+            const uint32_t d = (uint32_t)ui & 1u;
+            if (!warp_wait_bar(&bars[B_DFULL + d], (ui >> 1) & 1u, abort_flag)) { ok = false; break; }
+            tc_fence_after();
+            float v[NB];
+#pragma unroll
+            for (int c = 0; c < NB; c += 16) ld16(tbase + lane_off + d * 128u + (uint32_t)c, v + c);
+            tc_fence_before();
+            mbar_arrive(&bars[B_DEMPTY + d]);
+            // the staging tile is free once every epilogue thread has gathered the previous unit
+            if (ui >= 1 && !warp_wait_bar(&bars[B_GFREE], (ui - 1) & 1, abort_flag)) { ok = false; break; }
+#pragma unroll
+            for (int i = 0; i < PYB; ++i) gather[m * GP + i] = (v[i] + v[PYB + i]) * unscale;
+            mbar_arrive(&bars[B_GFULL]);
+            if (!warp_wait_bar(&bars[B_GFULL], ui & 1, abort_flag)) { ok = false; break; }
+            const int p0 = u * ppu;
+            for (int pl = 0; pl < ppu; ++pl) {
+                const int pair = p0 + pl;
+                if (pair >= npairs) break;
+                float* o = out + (size_t)pair * L;
+                for (int j = et; j < L; j += 128) {
+                    const float g = gather[(pl * ldp + m_jx[j]) * GP + m_ipy[j]];
+                    o[j] = scale ? g * scale[j] : g;
+                }
+            }
+            mbar_arrive(&bars[B_GFREE]);
+        }
+        if (!ok) fail(abort_flag, err, 4);
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1) {
+        __syncwarp();
+        tmem_dealloc(tbase, kTmemCols);
+    }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
+double by_value(int N, int p, int m) {
+    if (p == 0) return 1.0 / std::sqrt((double)N);
+    if (N % 2 == 0 && p == N - 1) return ((m & 1) ? -1.0 : 1.0) / std::sqrt((double)N);
+    const int j = (p + 1) / 2;
+    const long long r = ((long long)j * m) % N;
+    const double a = 2.0 * M_PI * (double)r / (double)N;
+    return std::sqrt(2.0 / N) * ((p & 1) ? std::cos(a) : std::sin(a));
+}
+
+// Plans of different shapes share a template instance, so its limit is the largest plan
+// of that instance (at most 227 KB).
+template <int NB>
+cudaError_t set_smem(uint32_t) {
+    return cudaFuncSetAttribute(fwd_ypass_tc_kernel<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem_plan(128, NB).total);
+}
+
+}  // namespace
+
+bool ytc_supported(const zl_plan_s& p, int ldp) {
+    return p.Py >= 1 && p.Py <= 64 && ldp % 4 == 0 && ldp <= 128 && encode_fn() != nullptr;
+}
+
+zl_status ytc_prepare(zl_plan_s& p, int ldp, cudaStream_t s) {
+    if (!ytc_supported(p, ldp)) return ZL_ERR_UNSUPPORTED;
+    YtcOperands* t = new YtcOperands();
+    t->pyb = (p.Py + 7) / 8 * 8;
+    const int nb = 2 * t->pyb;
+    t->nstage_y = (p.d.ny + YC - 1) / YC;
+    const int ppu = 128 / ldp;
+    t->smem = smem_plan(ppu * ldp, nb).total;
+    // kept y-frequencies in ascending order (the order of the byk table's columns)
+    std::vector<int> pylist;
+    {
+        std::vector<char> used(p.d.ny, 0);
+        for (int sidx : p.modes) used[sidx / p.d.nx] = 1;
+        for (int q = 0; q < p.d.ny; ++q)
+            if (used[q]) pylist.push_back(q);
+    }
+    const size_t yblocks = (size_t)t->nstage_y * (YC / YB);
+    const size_t per_block = (size_t)nb * 16;                       // FP16 elements per 8-row block
+    std::vector<__half> img(yblocks * per_block, __float2half_rn(0.f));
+    for (size_t yb = 0; yb < yblocks; ++yb)
+        for (int n = 0; n < nb; ++n) {
+            const int i = n % t->pyb, part = n / t->pyb;               // part 0: b_hi rows, 1: b_lo rows
+            for (int e = 0; e < YB; ++e) {
+                const int y = (int)yb * YB + e;
+                double b = 0.0;
+                if (y < p.d.ny && i < (int)pylist.size()) b = kBasisScale * by_value(p.d.ny, pylist[i], y);
+                const __half hi = __double2half(b);
+                const __half v = part == 0 ? hi : __double2half(b - (double)__half2float(hi));
+                for (int c = 0; c < 2; ++c) {
+                    const size_t off = yb * per_block * 2 + (size_t)(n >> 3) * 256 + (size_t)c * 128 + (size_t)(n & 7) * 16 +
+                                       (size_t)e * 2;
+                    img[off / 2] = v;
+                }
+            }
+        }
+    cudaError_t e = cudaMalloc(&t->bimg, img.size() * sizeof(__half));
+    if (e == cudaSuccess) e = cudaMalloc(&t->t1max, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMalloc(&t->d_err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(t->bimg, img.data(), img.size() * sizeof(__half), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(t->t1max, 0, sizeof(unsigned), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(t->d_err, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) {
+        switch (nb) {
+            case 16: e = set_smem<16>(t->smem); break;
+            case 32: e = set_smem<32>(t->smem); break;
+            case 48: e = set_smem<48>(t->smem); break;
+            case 64: e = set_smem<64>(t->smem); break;
+            case 80: e = set_smem<80>(t->smem); break;
+            case 96: e = set_smem<96>(t->smem); break;
+            case 112: e = set_smem<112>(t->smem); break;
+            case 128: e = set_smem<128>(t->smem); break;
+            default: e = cudaErrorInvalidValue;
+        }
+    }
+    if (e != cudaSuccess || t->smem > 227 * 1024) {
+        cudaFree(t->bimg);
+        cudaFree(t->t1max);
+        cudaFree(t->d_err);
+        delete t;
+        if (e == cudaErrorMemoryAllocation) return ZL_ERR_ALLOC;
+        return e == cudaSuccess ? ZL_ERR_UNSUPPORTED : ZL_ERR_CUDA;
+    }
+    p.ytc = t;
+    return ZL_OK;
+}
+
+void ytc_release(zl_plan_s& p) {
+    if (!p.ytc) return;
+    cudaFree(p.ytc->bimg);
+    cudaFree(p.ytc->t1max);
+    cudaFree(p.ytc->d_err);
+    delete p.ytc;
+    p.ytc = nullptr;
+}
+
+unsigned* ytc_max_word(const zl_plan_s& p) { return p.ytc ? p.ytc->t1max : nullptr; }
+
+cudaError_t ytc_read_error(const zl_plan_s& p, int* code) {
+    *code = 0;
+    if (!p.ytc) return cudaSuccess;
+    return cudaMemcpy(code, p.ytc->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+}
+
+cudaError_t ytc_clear_error(const zl_plan_s& p) {
+    if (!p.ytc) return cudaSuccess;
+    return cudaMemset(p.ytc->d_err, 0, sizeof(int));
+}
+
+cudaError_t forward_ypass_tc(const zl_plan_s& p, const float* t1, int ldp, const float* scale, float* out, int R,
+                             cudaStream_t s) {
+    const YtcOperands& t = *p.ytc;
+    const int npairs = R * p.d.K;
+    const int ppu = 128 / ldp, rows_u = ppu * ldp;
+    const int nb = 2 * t.pyb;
+    CUtensorMap tmap;
+    const cuuint64_t gdim[2] = {(cuuint64_t)npairs * ldp, (cuuint64_t)p.d.ny};
+    const cuuint64_t gstride[1] = {(cuuint64_t)npairs * ldp * sizeof(float)};
+    const cuuint32_t box[2] = {(cuuint32_t)rows_u, (cuuint32_t)YC};
+    const cuuint32_t estride[2] = {1, 1};
+    const CUresult cr = encode_fn()(&tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(t1), gdim, gstride, box,
+                                    estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (cr != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    const int units = (npairs + ppu - 1) / ppu;
+    const int grid = std::min(units, 148);
+    p.timer.begin(ZL_STAGE_FWD_YPASS, s);
+#define ZL_YTC_LAUNCH(NBV)                                                                                           \
+    fwd_ypass_tc_kernel<NBV><<<grid, kThreads, t.smem, s>>>(tmap, t.bimg, t.t1max, p.tf.m_ipy, p.tf.m_jx, scale, out, \
+                                                            t.d_err, npairs, ldp, ppu, p.L, t.nstage_y)
+    switch (nb) {
+        case 16: ZL_YTC_LAUNCH(16); break;
+        case 32: ZL_YTC_LAUNCH(32); break;
+        case 48: ZL_YTC_LAUNCH(48); break;
+        case 64: ZL_YTC_LAUNCH(64); break;
+        case 80: ZL_YTC_LAUNCH(80); break;
+        case 96: ZL_YTC_LAUNCH(96); break;
+        case 112: ZL_YTC_LAUNCH(112); break;
+        case 128: ZL_YTC_LAUNCH(128); break;
+        default: return cudaErrorInvalidValue;
+    }
+#undef ZL_YTC_LAUNCH
+    p.timer.end(s);
+    return cudaGetLastError();
+}
+
+}  // namespace zl

@@ -32,6 +32,7 @@ struct Tables {
 };
 
 struct TcOperands;   // tensor-core path state (k_tc.cu)
+struct YtcOperands;  // tensor-core y-pass state (k_ytc.cu)
 
 // Optional CUDA-event bracketing of every kernel stage (zl_set_stage_timing).
 struct StageTimer {
@@ -73,6 +74,7 @@ struct zl_plan_s {
     zl::Tables<double> td;
     zl::Tables<float> tf;
     zl::TcOperands* tc = nullptr;
+    zl::YtcOperands* ytc = nullptr;
     // zl_apply_left_inverse_host (allocated on first use): two device staging slots of
     // h_piece right-hand sides each for x and for x~, the copy-in and copy-out streams, and
     // per slot the events "copied in", "kernels done", "copied out"
@@ -152,5 +154,14 @@ cudaError_t forward_tc(const zl_plan_s& p, const float* x, float* out, int R, cu
 cudaError_t tc_read_error(const zl_plan_s& p, int* code);
 cudaError_t tc_clear_error(const zl_plan_s& p);
 
+// k_ytc.cu: tensor-core y-pass of the mixed left inverse (t1 from the tensor-core column kernel)
+bool ytc_supported(const zl_plan_s& p, int ldp);
+zl_status ytc_prepare(zl_plan_s& p, int ldp, cudaStream_t s);
+void ytc_release(zl_plan_s& p);
+unsigned* ytc_max_word(const zl_plan_s& p);
+cudaError_t ytc_read_error(const zl_plan_s& p, int* code);
+cudaError_t ytc_clear_error(const zl_plan_s& p);
+cudaError_t forward_ypass_tc(const zl_plan_s& p, const float* t1, int ldp, const float* scale, float* out, int R,
+                             cudaStream_t s);
 
 }  // namespace zl
