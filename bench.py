@@ -48,6 +48,12 @@ def parse_args():
     ap.add_argument("--prec", default=None, choices=["fp64", "fp32", "mixed"])
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--op", choices=["left_inverse", "gradient"], default="left_inverse",
+                    help="gradient: a step is the gradient of J = 1/2 ||Zh^- x||^2, i.e. the left inverse followed "
+                         "by the adjoint (the 512x512x16 differentiation workload)")
+    ap.add_argument("--partition", choices=["replicas", "slabs"], default="replicas",
+                    help="replicas: every rank an independent batch (weak scaling); slabs: the ranks split the "
+                         "grid rows of one batch and all-reduce the K L partial sums (strong scaling)")
     ap.add_argument("--fp64-steps", type=int, default=5,
                     help="timed steps of the plain FP64 GPU form of the same workload (0: skip)")
     return ap.parse_args()
@@ -69,6 +75,13 @@ def reduce_max(value, device):
     t = torch.tensor([float(value)], device=device, dtype=torch.float64)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def slab_rows(ny, world, rank):
+    """Rows [y0, y1) of rank `rank` when `world` ranks split ny grid rows as evenly as possible."""
+    base, extra = divmod(ny, world)
+    y0 = rank * base + min(rank, extra)
+    return y0, y0 + base + (1 if rank < extra else 0)
 
 
 def aggregate_value(world, steps, R, seconds):
@@ -407,6 +420,154 @@ def fp64_gpu_form(w, R, rank, dev, steps, stream):
             "what": "ZL_FP64 plan (FP64 CUDA-core kernels) on the same workload, this GPU; ratio = value / this"}
 
 
+def run_slabs(args, w, prec):
+    """The y-slab partition of the paper's parallel decomposition: rank r holds grid rows
+    slab_rows(ny, N, r) of the ensemble's and the right-hand sides' segments, computes its
+    unscaled partial sums (zl_apply_left_inverse_rows), the ranks add them with one NCCL
+    all-reduce of K L values per right-hand side, and every rank scales the sum
+    (zl_scale_modes).  A step is one batch of R right-hand sides through all of it."""
+    import torch
+    world, rank, local = dist_env()
+    from paper_2609_13327_b300 import zl
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    R = w.R
+    sdt = synth.storage_dtype(prec)
+    y0, y1 = slab_rows(w.Ny, world, rank)
+    Z = torch.from_numpy(synth.ensemble(w).astype(sdt)).to(dev)
+    lam = zl.zl_gaussian_spectrum(w.Nx, w.Ny, w.ell_loc)
+    t0 = time.perf_counter()
+    plan = zl.zl_setup(Z, lam, tau=w.tau, prec=prec, max_rhs=R, nx=w.Nx, ny=w.Ny)
+    setup_s = time.perf_counter() - t0
+    del Z
+    x = synth.rhs(w, R=R, dtype=sdt)
+    xs = torch.from_numpy(np.ascontiguousarray(x[:, :, y0 * w.Nx:y1 * w.Nx])).to(dev)
+    part = torch.empty((R, w.K, plan.L), dtype=xs.dtype, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        if y1 > y0:
+            zl.zl_apply_left_inverse_rows(plan, y0, y1, xs, part, stream)
+        else:                                   # more ranks than grid rows: this one adds nothing
+            part.zero_()
+        if dist is not None:
+            dist.all_reduce(part)
+        zl.zl_scale_modes(plan, part, part, stream)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ms = reduce_max(ev0.elapsed_time(ev1), dev)
+    value = args.steps * R / (ms / 1e3)
+    line = {"metric": "left-inverse applications/s", "value": value, "unit": "vectors/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "strong", "vs_baseline": None,
+            "dtype": "f16x3 split, f32 accumulate" if prec == "mixed" else ("f64" if prec == "fp64" else "f32"),
+            "data": "synthetic (seeded Gaussian-correlated ensemble, N(0,1) right-hand sides)",
+            "config": dict(workload_config(w, plan.L, prec, R), partition=f"{world} y-slabs, one all-reduce of "
+                                                                        f"K L values per right-hand side"),
+            "setup_s": setup_s, "gpu_launches": None}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle import compare
+        _, ref = cpu_baseline(w, prec, x[:2].astype(np.float64))
+        line["accuracy"] = {"max_rel_err_vs_fp64_oracle": compare.measures(part[:2].cpu().numpy(), ref, 2)[0],
+                            "rhs_checked": 2}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.destroy()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def run_gradient(args, w, prec):
+    """Gradient of J(x) = 1/2 ||Zh^- x||^2 for a batch of R right-hand sides: x~ = Zh^- x
+    (left inverse) then g = (Zh^-)^T x~ (adjoint kernels); replicas under torchrun."""
+    import torch
+    world, rank, local = dist_env()
+    from paper_2609_13327_b300 import zl
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    R = w.R
+    sdt = synth.storage_dtype(prec)
+    Z = torch.from_numpy(synth.ensemble(w).astype(sdt)).to(dev)
+    lam = zl.zl_gaussian_spectrum(w.Nx, w.Ny, w.ell_loc)
+    t0 = time.perf_counter()
+    plan = zl.zl_setup(Z, lam, tau=w.tau, prec=prec, max_rhs=R, nx=w.Nx, ny=w.Ny)
+    setup_s = time.perf_counter() - t0
+    del Z
+    x = torch.from_numpy(synth.rhs(w, R=R, seed=w.seed + 1000 * rank, dtype=sdt)).to(dev)
+    xt = torch.empty((R, w.K, plan.L), dtype=x.dtype, device=dev)
+    g = torch.empty_like(x)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        zl.zl_apply_left_inverse(plan, x, xt, stream)
+        zl.zl_apply_adjoint(plan, xt, g, stream)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    plan.set_stage_timing(True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    plan.set_stage_timing(False)
+    ms = reduce_max(ev0.elapsed_time(ev1), dev)
+    stages = plan.stage_times()
+    value = aggregate_value(world, args.steps, R, ms / 1e3)
+    sx, sz = element_sizes(prec)
+    # read x, write x~, read x~, write g; the ensemble operand once per batch in each direction
+    bpr = sx * (2 * w.n + 2 * w.K * plan.L) + 2 * sz * w.n * w.K / R
+    peak, peak_kind = measured_peak_hbm()
+    line = {"metric": "gradient applications/s", "value": value, "unit": "vectors/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if prec == "fp64" else ("f16x3 split, f32 accumulate (left inverse)" if plan_uses_tc(plan) else "f32"),
+            "data": "synthetic (seeded Gaussian-correlated ensemble, N(0,1) right-hand sides)",
+            "config": dict(workload_config(w, plan.L, prec, R), op="gradient of 1/2 ||Zh^- x||^2 (left inverse + adjoint)"),
+            "setup_s": setup_s,
+            "roofline": {"bound": "hbm", "step_frac": bpr * R / (ms / args.steps / 1e3) / 1e9 / peak, "peak": peak,
+                         "unit": "GB/s", "peak_source": peak_kind,
+                         "stages_ms_per_launch": {k: (v[1] / v[0] if v[0] else None) for k, v in stages.items()}},
+            "gpu_launches": sum(n for n, _ in stages.values())}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle import compare, swift
+        plan_o, _ = oracle_plan(w, prec)
+        xs = x[:2].cpu().numpy().astype(np.float64)
+        ref = swift.apply_adjoint(plan_o, swift.apply_left_inverse(plan_o, xs))
+        line["accuracy"] = {"max_rel_err_vs_fp64_oracle": compare.measures(g[:2].cpu().numpy(), ref, 1)[0],
+                            "rhs_checked": 2}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.destroy()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
 def plan_uses_tc(plan):
     return getattr(plan, "uses_tc", lambda: False)()
 
@@ -430,23 +591,30 @@ def run_batched(args, prec):
     dev = torch.device("cuda", local)
     ws = synth.batched_instances()
     sdt = synth.storage_dtype(prec)
-    t0 = time.perf_counter()
     # an instance whose draw has a rank-deficient column (the library reports ZL_ERR_RANK and
-    # which instance) gets a new ensemble draw; the redraws are counted in the JSON line
+    # which instance) gets a new ensemble draw; the redraws are counted in the JSON line.
+    # setup_s times the library's setup only (not the host's synthetic draws).
     redrawn = {}
+    ens = {}
     while True:
-        insts = [{"Z": torch.from_numpy(synth.ensemble(w, seed=w.seed + 1000003 * redrawn.get(i, 0)).astype(sdt)).to(dev),
+        for i, w in enumerate(ws):
+            key = (i, redrawn.get(i, 0))
+            if key not in ens:
+                ens[key] = synth.ensemble(w, seed=w.seed + 1000003 * redrawn.get(i, 0)).astype(sdt)
+        insts = [{"Z": torch.from_numpy(ens[(i, redrawn.get(i, 0))]).to(dev),
                   "spectrum": zl.zl_gaussian_spectrum(w.Nx, w.Ny, w.ell_loc), "nx": w.Nx, "ny": w.Ny, "prec": prec,
                   "tau": w.tau, "max_rhs": w.R} for i, w in enumerate(ws)]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
         try:
             batch = zl.zl_setup_batch(insts)
+            torch.cuda.synchronize()
+            setup_s = time.perf_counter() - t0
             break
         except zl.ZLError as err:
             if err.code != zl.ZL_ERR_RANK or err.failed_instance < 0 or redrawn.get(err.failed_instance, 0) >= 3:
                 raise
             redrawn[err.failed_instance] = redrawn.get(err.failed_instance, 0) + 1
-    torch.cuda.synchronize()
-    setup_s = time.perf_counter() - t0
     del insts
     xs = [torch.from_numpy(synth.rhs(w, seed=w.seed + 1000 * rank, dtype=sdt)).to(dev) for w in ws]
     outs = [torch.empty((x.shape[0], p.K, p.L), dtype=x.dtype, device=dev) for x, p in zip(xs, batch.plans)]
@@ -591,6 +759,10 @@ def main():
     prec = args.prec or w.prec
     if args.impl == "reference":
         run_reference(args, w, prec)
+    elif args.partition == "slabs":
+        run_slabs(args, w, prec)
+    elif args.op == "gradient":
+        run_gradient(args, w, prec)
     else:
         run_ours(args, w, prec)
 

@@ -115,6 +115,9 @@ zl_status zl_setup(const zl_desc* desc, const void* Z, const double* spectrum,
  */
 zl_status zl_get_info(zl_plan plan, int* L, int* nw, int* K, long long* nh, int* bad_column);
 
+/* zl_get_desc -- the plan's descriptor (as given to zl_setup or stored by zl_plan_save). */
+zl_status zl_get_desc(zl_plan plan, zl_desc* desc);
+
 /*
  * zl_get_runtime_info -- which kernel path the plan's left inverse takes and
  * whether a device-side wait has given up.  Either pointer may be NULL.
@@ -145,6 +148,20 @@ zl_status zl_get_runtime_info(zl_plan plan, int* tensor_core_path, int* device_e
  * 1), ZL_ERR_UNSUPPORTED (the plan has no tensor-core path), ZL_ERR_CUDA.
  */
 zl_status zl_set_test_wait_timeout(zl_plan plan, int enable);
+
+/*
+ * zl_set_test_alloc_failure -- a test hook of the error paths; the paper has no
+ * counterpart.  n > 0: the n-th device allocation the library makes from now on
+ * (setup, batch setup, host staging) fails as if the device were full, and the
+ * call that made it returns ZL_ERR_ALLOC after releasing everything it had
+ * allocated; n = 0 switches the hook off.  Process-wide.  Errors: ZL_ERR_ARG
+ * (n < 0).
+ *
+ * Logging: when the environment variable ZL_LOG is set (and not "0") at the
+ * first apply, every apply writes one JSON line to stderr with the operator,
+ * R, the sizes, the precision and the column and y-pass kernels it runs.
+ */
+zl_status zl_set_test_alloc_failure(int n);
 
 /*
  * zl_get_modes -- the kept packed mode indices s (ascending), host int[L].
@@ -353,6 +370,26 @@ zl_status zl_xi_indicators(const double* M, int n, double* out, void* stream);
  * Errors: ZL_ERR_ARG, ZL_ERR_CUDA.
  */
 zl_status zl_delta(zl_plan plan, const void* xt, const void* back, void* d, double* norms, int R, void* stream);
+
+/*
+ * zl_plan_save / zl_plan_load -- checkpoint a plan and restore it without
+ * redoing the setup's per-column factorisation (the paper has no counterpart).
+ * The file holds the descriptor, the kept modes and their eigenvalues, the
+ * rank status, the plan's copy of Z and the pseudo-inverse P (its storage
+ * precision: 2 K n_w n_h elements, about 1 GB at 256x256x32, K = 64, FP32), in
+ * this build's native layout (not portable across builds or byte orders).
+ * zl_plan_load validates the header (magic, sizes, ascending modes, positive
+ * eigenvalues) and rejects any mismatch or short file with ZL_ERR_ARG before
+ * touching the device; it then builds the tables and the tensor-core operands
+ * from the stored P and returns a plan whose applies give the same bits as the
+ * saved plan's (ZL_ERR_RANK with a valid plan when the saved plan was
+ * rank-deficient).  Both synchronise: save reads the device buffers, load uses
+ * `stream` and synchronises it.  Errors: ZL_ERR_ARG (null arguments, an
+ * unreadable or unwritable file, a malformed header), ZL_ERR_ALLOC,
+ * ZL_ERR_CUDA.
+ */
+zl_status zl_plan_save(zl_plan plan, const char* path);
+zl_status zl_plan_load(const char* path, void* stream, zl_plan* out);
 
 /* zl_destroy -- free a plan and everything it owns (NULL is a no-op).  The
  * caller must make sure no queued apply still uses it. */

@@ -123,6 +123,7 @@ enum {
     B_D1EMPTY = B_B1FULL + 2,
     B_WFULL,
     B_D2EMPTY,
+    B_STG,                             // the epilogue warps have left the W buffer (D2 staging)
     B_FIN,
     B_COUNT
 };
@@ -252,6 +253,7 @@ fwd_column_tc_kernel(const __grid_constant__ CUtensorMap tmap_x, const __half* _
         mbar_init(&bars[B_D1EMPTY], kEpiThreads);
         mbar_init(&bars[B_WFULL], kEpiThreads);
         mbar_init(&bars[B_D2EMPTY], kEpiThreads);
+        mbar_init(&bars[B_STG], kEpiThreads);
         mbar_init(&bars[B_FIN], 1);
         *abort_flag = 0;
         fence_mbar_init();
@@ -430,15 +432,21 @@ fwd_column_tc_kernel(const __grid_constant__ CUtensorMap tmap_x, const __half* _
             return true;
         };
 
-        // D2 of a finished unit (its last x-pass has completed): rows (r, k) -> t1[y][r0 + r][k][0..pxp)
+        // D2 of a finished unit (its last x-pass has completed): rows (r, k) -> t1[y][r0 + r][k][0..pxp).
+        // A warp's 32 rows of a tile are one member block of one rhs, i.e. 32 consecutive rows of
+        // t1: each lane puts its row into the warp's staging area (the W buffer is free here: the
+        // x-pass that read it has completed) and the warp then writes the block with coalesced
+        // 16-byte stores.
         auto drain_d2 = [&](uint32_t gl) -> bool {
             const int u = (int)blockIdx.x + (int)(gl / G) * (int)gridDim.x;
             const int y = u / n_rc, r0 = (u % n_rc) * RC;
+            float4* stg = reinterpret_cast<float4*>(sw + (uint32_t)ew * 32u * (uint32_t)pxp * 4u);
+            const int q4 = pxp / 4;                                  // float4 per row
             tc_fence_after();
 #pragma unroll 1
             for (int t = rset; t < MT; t += 2) {
-                const int row = 128 * t + 32 * q + lane;
-                const int r = row >> 6, k = row & 63;
+                const int row0 = 128 * t + 32 * q;                   // the warp's first row
+                const int r = row0 >> 6, k0 = row0 & 63;             // one rhs, members k0 .. k0 + 31
                 static_assert(N2 == 48, "three 16-column TMEM loads per row");
                 uint32_t d0[16], d1[16], d2[16];
                 tmem_ld16(tbase + lane_off + (uint32_t)(t * N2), d0);
@@ -448,9 +456,11 @@ fwd_column_tc_kernel(const __grid_constant__ CUtensorMap tmap_x, const __half* _
                 tmem_regs_ready(d0);
                 tmem_regs_ready(d1);
                 tmem_regs_ready(d2);
+                const int nk = min(32, K - k0);                      // member rows of this block that exist
+                const bool live = r0 + r < R && nk > 0;
                 if (t1max != nullptr) {   // max |t1| of the launch, for the y-pass's FP16 scaling
                     float mx = 0.f;
-                    if (r0 + r < R && k < K)
+                    if (live && lane < nk)
 #pragma unroll
                         for (int i = 0; i < 16; ++i)
                             mx = fmaxf(mx, fmaxf(fabsf(__uint_as_float(d0[i])),
@@ -459,12 +469,12 @@ fwd_column_tc_kernel(const __grid_constant__ CUtensorMap tmap_x, const __half* _
                     for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
                     if (lane == 0) atomicMax(t1max, __float_as_uint(mx));
                 }
-                if (r0 + r < R && k < K) {
-                    float4* dst = reinterpret_cast<float4*>(t1 + (((size_t)y * R + r0 + r) * K + k) * pxp);
+                if (live) {
+                    float4* mine = stg + lane * q4;
                     auto put = [&](int c, const uint32_t (&d)[16], int i) {
-                        if (4 * c < pxp)
-                            dst[c] = make_float4(__uint_as_float(d[i]), __uint_as_float(d[i + 1]), __uint_as_float(d[i + 2]),
-                                                 __uint_as_float(d[i + 3]));
+                        if (c < q4)
+                            mine[c] = make_float4(__uint_as_float(d[i]), __uint_as_float(d[i + 1]), __uint_as_float(d[i + 2]),
+                                                  __uint_as_float(d[i + 3]));
                     };
 #pragma unroll
                     for (int c = 0; c < 4; ++c) {
@@ -472,6 +482,10 @@ fwd_column_tc_kernel(const __grid_constant__ CUtensorMap tmap_x, const __half* _
                         put(4 + c, d1, 4 * c);
                         put(8 + c, d2, 4 * c);
                     }
+                    __syncwarp();
+                    float4* dst = reinterpret_cast<float4*>(t1 + (((size_t)y * R + r0 + r) * K + k0) * pxp);
+                    for (int i = lane; i < nk * q4; i += 32) dst[i] = stg[i];
+                    __syncwarp();
                 }
             }
             tc_fence_before();
@@ -509,7 +523,7 @@ fwd_column_tc_kernel(const __grid_constant__ CUtensorMap tmap_x, const __half* _
         // One iteration per group, both V1 half-groups in sequence (the sums of the first
         // half-group never cross a loop iteration).
         bool pending = false;                          // a finished unit whose D2 is still to be drained
-        uint32_t pending_g = 0;
+        uint32_t pending_g = 0, ndrain = 0;
         for (uint32_t g = 0; g < total_groups && ok; ++g) {
             float s0[HG][8], s1[HG][8];                // w of this lane: column x rhs (8 of the unit's 16)
             // ---- first half-group: columns 0-3
@@ -524,6 +538,10 @@ fwd_column_tc_kernel(const __grid_constant__ CUtensorMap tmap_x, const __half* _
             if (pending) {
                 if (!drain_d2(pending_g)) { ok = false; break; }
                 pending = false;
+                // the D2 staging used the W buffer: every epilogue warp must be done with it
+                mbar_arrive(&bars[B_STG]);
+                if (!warp_wait_bar(&bars[B_STG], ndrain & 1u, abort_flag)) { ok = false; break; }
+                ++ndrain;
             }
             // ---- W of group g: rows (r, k), 8 columns per 16-byte row in each K-chunk
 #pragma unroll
@@ -635,9 +653,9 @@ zl_status tc_prepare(zl_plan_s& p, cudaStream_t s) {
     cudaError_t e = cudaSuccess;
     const size_t pimg_bytes = (size_t)p.nh * 256u * t->nwp;
     const size_t bx_bytes = (size_t)(nx / GC) * kBxStage;
-    e = cudaMalloc(&t->pimg, pimg_bytes);
-    if (e == cudaSuccess) e = cudaMalloc(&t->bximg, bx_bytes);
-    if (e == cudaSuccess) e = cudaMalloc(&t->d_err, sizeof(int));
+    e = zl::dev_malloc((void**)&t->pimg, pimg_bytes);
+    if (e == cudaSuccess) e = zl::dev_malloc((void**)&t->bximg, bx_bytes);
+    if (e == cudaSuccess) e = zl::dev_malloc((void**)&t->d_err, sizeof(int));
     if (e == cudaSuccess) e = cudaMemsetAsync(t->pimg, 0, pimg_bytes, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(t->d_err, 0, sizeof(int), s);
     if (e == cudaSuccess) {
@@ -665,7 +683,7 @@ zl_status tc_prepare(zl_plan_s& p, cudaStream_t s) {
     // t1 rows are padded to pxp for 16-byte stores
     if (e == cudaSuccess && t->pxp != p.Px) {
         void* t1 = nullptr;
-        e = cudaMalloc(&t1, (size_t)p.d.max_rhs * p.d.K * p.d.ny * t->pxp * sizeof(float));
+        e = zl::dev_malloc((void**)&t1, (size_t)p.d.max_rhs * p.d.K * p.d.ny * t->pxp * sizeof(float));
         if (e == cudaSuccess) {
             cudaFree(p.t1);
             p.t1 = t1;

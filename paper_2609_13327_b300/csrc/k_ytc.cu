@@ -40,6 +40,7 @@ struct YtcOperands {
     int* d_err = nullptr;
     int pyb = 0;               // kept y-frequencies rounded up to 8
     int nstage_y = 0;          // stages of 32 rows of y covering ny
+    int resident = 0;          // 1: the whole basis image stays in shared memory
     uint32_t smem = 0;
 };
 
@@ -59,21 +60,26 @@ constexpr float kBasisScale = 16.0f;
 constexpr unsigned long long kWaitCycles = 4000000000ull;
 
 enum { B_FULL = 0, B_EMPTY = B_FULL + S, B_AFULL = B_EMPTY + S, B_DFULL = B_AFULL + SA,
-       B_DEMPTY = B_DFULL + 2, B_GFULL = B_DEMPTY + 2, B_GFREE, B_FIN, B_COUNT };
+       B_DEMPTY = B_DFULL + 2, B_GFULL = B_DEMPTY + 2, B_GFREE, B_BASIS, B_FIN, B_COUNT };
 
 struct Plan {
-    uint32_t stage_t, stage_b, stage, ring, aring, gather, bars, total;
+    uint32_t stage_t, stage_b, stage, ring, basis, aring, gather, bars, total;
 };
 
-// rows_u = ppu * ldp rows of t1 per stage row of y; nb = N = 2 * pyb
-__host__ __device__ inline Plan smem_plan(int rows_u, int nb) {
+// rows_u = ppu * ldp rows of t1 per stage row of y; nb = N = 2 * pyb.  resident > 0: the
+// basis of all `resident` stages of y stays in shared memory (loaded once per CTA) and a
+// stage holds t1 only; resident == 0: every stage carries its rows of the basis.
+__host__ __device__ inline Plan smem_plan(int rows_u, int nb, int resident) {
     Plan s{};
     s.stage_t = ((uint32_t)rows_u * YC * 4u + 1023u) & ~1023u;
     s.stage_b = (uint32_t)(YC / YB) * (uint32_t)nb * 32u;
-    s.stage = (s.stage_t + s.stage_b + 1023u) & ~1023u;
+    s.stage = resident > 0 ? s.stage_t : (s.stage_t + s.stage_b + 1023u) & ~1023u;
     uint32_t o = 0;
     s.ring = o;
     o += S * s.stage;
+    s.basis = o;
+    o += (uint32_t)resident * s.stage_b;
+    o = (o + 1023u) & ~1023u;
     s.aring = o;
     o += SA * kASlot;
     s.gather = o;
@@ -129,11 +135,11 @@ __global__ void __launch_bounds__(kThreads, 1)
 fwd_ypass_tc_kernel(const __grid_constant__ CUtensorMap tmap_t, const __half* __restrict__ bimg,
                     const unsigned* __restrict__ t1max, const int* __restrict__ m_ipy, const int* __restrict__ m_jx,
                     const float* __restrict__ scale, float* __restrict__ out, int* __restrict__ err, int npairs,
-                    int ldp, int ppu, int L, int nstage_y) {
+                    int ldp, int ppu, int L, int nstage_y, int resident) {
     constexpr int PYB = NB / 2;
     extern __shared__ __align__(1024) uint8_t smem[];
     const int rows_u = ppu * ldp;
-    const Plan sp = smem_plan(rows_u, NB);
+    const Plan sp = smem_plan(rows_u, NB, resident ? nstage_y : 0);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + sp.bars);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + B_COUNT);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
@@ -155,6 +161,7 @@ fwd_ypass_tc_kernel(const __grid_constant__ CUtensorMap tmap_t, const __half* __
         }
         mbar_init(&bars[B_GFULL], 128);
         mbar_init(&bars[B_GFREE], 128);
+        mbar_init(&bars[B_BASIS], 1);
         mbar_init(&bars[B_FIN], 1);
         *abort_flag = 0;
         fence_mbar_init();
@@ -168,27 +175,47 @@ fwd_ypass_tc_kernel(const __grid_constant__ CUtensorMap tmap_t, const __half* __
 
     if (warp == 0) {
         // ------------------------------------------------------------ producer
-        if (lane == 0) {
-            uint32_t sc = 0;
+        // Lanes 0 and 1 issue the copies of even and odd stages: a copy costs its issuing
+        // thread a roughly fixed time, so two threads keep twice the bytes in flight.
+        if (lane < 2) {
+            if (resident && lane == 0) {
+                const uint32_t bytes = (uint32_t)nstage_y * sp.stage_b;
+                mbar_arrive_expect_tx(&bars[B_BASIS], bytes);
+                for (int st = 0; st < nstage_y; ++st)
+                    bulk_g2s(smem + sp.basis + (uint32_t)st * sp.stage_b, bimg + (size_t)st * (sp.stage_b / 2), sp.stage_b,
+                             &bars[B_BASIS]);
+            }
+            uint32_t sc = 0, mine = 0;
             for (int ui = 0; ui < my_units && !*abort_flag; ++ui) {
                 const int u = (int)blockIdx.x + ui * (int)gridDim.x;
                 for (int st = 0; st < nstage_y; ++st, ++sc) {
+                    if ((int)(sc & 1u) != lane) continue;
                     const uint32_t s = sc % S;
                     if (sc >= S && !wait_bar(&bars[B_EMPTY + s], ((sc / S) - 1) & 1u, abort_flag)) {
                         fail(abort_flag, err, 1);
                         break;
                     }
                     uint8_t* dst = smem + sp.ring + s * sp.stage;
-                    mbar_arrive_expect_tx(&bars[B_FULL + s], tbytes + sp.stage_b);
+                    mbar_arrive_expect_tx(&bars[B_FULL + s], tbytes + (resident ? 0u : sp.stage_b));
                     tma_load_2d(dst, &tmap_t, u * rows_u, st * YC, &bars[B_FULL + s]);
-                    bulk_g2s(dst + sp.stage_t, bimg + (size_t)st * (sp.stage_b / 2), sp.stage_b, &bars[B_FULL + s]);
+                    if (!resident)
+                        bulk_g2s(dst + sp.stage_t, bimg + (size_t)st * (sp.stage_b / 2), sp.stage_b, &bars[B_FULL + s]);
+                    ++mine;
                 }
             }
-            // every issued copy lands before the CTA exits
-            for (uint32_t s = 0; s < S && s < sc; ++s) {
-                const uint32_t n = (sc - s + S - 1) / S;
+            // every copy this lane issued lands before the CTA exits: its copies are the stages
+            // lane + 2 i (i < mine), alternating between its two slots, so the last two are the
+            // last ones into each of them
+            static_assert(S == 4, "two slots per issuing lane");
+            for (uint32_t i = mine > 2 ? mine - 2 : 0; i < mine; ++i) {
+                const uint32_t c = (uint32_t)lane + 2u * i;
                 const long long t0 = clock64();
-                while (!mbar_try_wait(&bars[B_FULL + s], (n - 1) & 1u) && (unsigned long long)(clock64() - t0) < kWaitCycles) {}
+                while (!mbar_try_wait(&bars[B_FULL + c % S], (c / S) & 1u) &&
+                       (unsigned long long)(clock64() - t0) < kWaitCycles) {}
+            }
+            if (resident && lane == 0) {
+                const long long t0 = clock64();
+                while (!mbar_try_wait(&bars[B_BASIS], 0) && (unsigned long long)(clock64() - t0) < kWaitCycles) {}
             }
         }
     } else if (warp == 1) {
@@ -196,8 +223,10 @@ fwd_ypass_tc_kernel(const __grid_constant__ CUtensorMap tmap_t, const __half* __
         if (lane == 0) {
             constexpr uint32_t idesc = idesc_f16_f32(128, NB);
             const uint64_t dA0 = smem_desc(smem_u32(smem + sp.aring), 128u, 256u);
-            const uint64_t dB0 = smem_desc(smem_u32(smem + sp.ring + sp.stage_t), 128u, 256u);
+            const uint64_t dB0 = resident ? smem_desc(smem_u32(smem + sp.basis), 128u, 256u)
+                                          : smem_desc(smem_u32(smem + sp.ring + sp.stage_t), 128u, 256u);
             bool ok = true;
+            if (resident && !wait_bar(&bars[B_BASIS], 0, abort_flag)) ok = false;
             uint32_t sc = 0;
             for (int ui = 0; ui < my_units && ok; ++ui) {
                 const uint32_t d = (uint32_t)ui & 1u;
@@ -212,7 +241,8 @@ fwd_ypass_tc_kernel(const __grid_constant__ CUtensorMap tmap_t, const __half* __
                         if (!wait_bar(&bars[B_AFULL + a], (sc >> 1) & 1u, abort_flag)) { ok = false; break; }
                         tc_fence_after();
                         const uint64_t da = dA0 + ((a * kASlot) >> 4);
-                        const uint64_t db = dB0 + ((s * sp.stage + (uint32_t)b * NB * 32u) >> 4);
+                        const uint32_t boff = resident ? (uint32_t)st * sp.stage_b : s * sp.stage;
+                        const uint64_t db = dB0 + ((boff + (uint32_t)b * NB * 32u) >> 4);
                         mma_f16(tbase + d * 128u, da, db, idesc, (st > 0 || b > 0) ? 1u : 0u);
                     }
                     // one commit per stage frees its T block, its basis and its A group
@@ -348,12 +378,11 @@ double by_value(int N, int p, int m) {
     return std::sqrt(2.0 / N) * ((p & 1) ? std::cos(a) : std::sin(a));
 }
 
-// Plans of different shapes share a template instance, so its limit is the largest plan
-// of that instance (at most 227 KB).
+// Plans of different shapes share a template instance, so its limit is the largest that a
+// plan may use (227 KB).
 template <int NB>
 cudaError_t set_smem(uint32_t) {
-    return cudaFuncSetAttribute(fwd_ypass_tc_kernel<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem_plan(128, NB).total);
+    return cudaFuncSetAttribute(fwd_ypass_tc_kernel<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
 }
 
 }  // namespace
@@ -369,7 +398,8 @@ zl_status ytc_prepare(zl_plan_s& p, int ldp, cudaStream_t s) {
     const int nb = 2 * t->pyb;
     t->nstage_y = (p.d.ny + YC - 1) / YC;
     const int ppu = 128 / ldp;
-    t->smem = smem_plan(ppu * ldp, nb).total;
+    t->resident = smem_plan(ppu * ldp, nb, t->nstage_y).total <= 227u * 1024u ? 1 : 0;
+    t->smem = smem_plan(ppu * ldp, nb, t->resident ? t->nstage_y : 0).total;
     // kept y-frequencies in ascending order (the order of the byk table's columns)
     std::vector<int> pylist;
     {
@@ -397,9 +427,9 @@ zl_status ytc_prepare(zl_plan_s& p, int ldp, cudaStream_t s) {
                 }
             }
         }
-    cudaError_t e = cudaMalloc(&t->bimg, img.size() * sizeof(__half));
-    if (e == cudaSuccess) e = cudaMalloc(&t->t1max, sizeof(unsigned));
-    if (e == cudaSuccess) e = cudaMalloc(&t->d_err, sizeof(int));
+    cudaError_t e = zl::dev_malloc((void**)&t->bimg, img.size() * sizeof(__half));
+    if (e == cudaSuccess) e = zl::dev_malloc((void**)&t->t1max, sizeof(unsigned));
+    if (e == cudaSuccess) e = zl::dev_malloc((void**)&t->d_err, sizeof(int));
     if (e == cudaSuccess) e = cudaMemcpyAsync(t->bimg, img.data(), img.size() * sizeof(__half), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(t->t1max, 0, sizeof(unsigned), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(t->d_err, 0, sizeof(int), s);
@@ -471,7 +501,7 @@ cudaError_t forward_ypass_tc(const zl_plan_s& p, const float* t1, int ldp, const
     p.timer.begin(ZL_STAGE_FWD_YPASS, s);
 #define ZL_YTC_LAUNCH(NBV)                                                                                           \
     fwd_ypass_tc_kernel<NBV><<<grid, kThreads, t.smem, s>>>(tmap, t.bimg, t.t1max, p.tf.m_ipy, p.tf.m_jx, scale, out, \
-                                                            t.d_err, npairs, ldp, ppu, p.L, t.nstage_y)
+                                                            t.d_err, npairs, ldp, ppu, p.L, t.nstage_y, t.resident)
     switch (nb) {
         case 16: ZL_YTC_LAUNCH(16); break;
         case 32: ZL_YTC_LAUNCH(32); break;

@@ -3,7 +3,9 @@
 #include "zl_internal.cuh"
 
 #include <algorithm>
+#include <atomic>
 #include <climits>
+#include <cstdio>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -61,7 +63,7 @@ std::vector<double> gaussian_axis_spectrum(int N, double ell) {
 
 template <typename T>
 cudaError_t upload(T** dst, const std::vector<T>& src, cudaStream_t s) {
-    cudaError_t e = cudaMalloc((void**)dst, std::max<size_t>(1, src.size()) * sizeof(T));
+    cudaError_t e = zl::dev_malloc((void**)dst, std::max<size_t>(1, src.size()) * sizeof(T));
     if (e != cudaSuccess) return e;
     if (src.empty()) return cudaSuccess;
     e = cudaMemcpyAsync(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, s);
@@ -178,6 +180,25 @@ bool valid_plan(zl_plan p) { return p != nullptr && p->P != nullptr; }
 // Operator kinds for the shared forward / inverse passes.
 enum class Op { LeftInverse, SqrtAdjoint, Sqrt, Adjoint };
 
+// ZL_LOG (environment, read once): when set and not "0", every apply writes one JSON line
+// to stderr with the operator, the sizes and the kernels it runs.
+bool log_enabled() {
+    static const bool on = [] {
+        const char* v = std::getenv("ZL_LOG");
+        return v != nullptr && *v != '\0' && std::strcmp(v, "0") != 0;
+    }();
+    return on;
+}
+
+void log_call(const char* op, const zl_plan_s* p, int R, const char* column, const char* ypass) {
+    if (!log_enabled()) return;
+    static const char* const prec[] = {"fp64", "fp32", "mixed"};
+    std::fprintf(stderr,
+                 "{\"zl\": \"%s\", \"R\": %d, \"nx\": %d, \"ny\": %d, \"nw\": %d, \"K\": %d, \"L\": %d, "
+                 "\"prec\": \"%s\", \"column\": \"%s\", \"ypass\": \"%s\"}\n",
+                 op, R, p->d.nx, p->d.ny, p->d.nw, p->d.K, p->L, prec[(int)p->d.prec], column, ypass);
+}
+
 zl_status run(zl_plan p, Op op, const void* in, void* out, int R, void* stream) {
     if (!valid_plan(p) || (R > 0 && (in == nullptr || out == nullptr)) || R < 0) return ZL_ERR_ARG;
     if (p->bad_column >= 0) return ZL_ERR_RANK;
@@ -188,6 +209,11 @@ zl_status run(zl_plan p, Op op, const void* in, void* out, int R, void* stream) 
     const long long ns = (long long)p->d.K * p->L;
     const bool fwd = (op == Op::LeftInverse || op == Op::SqrtAdjoint);
     const long long in_len = fwd ? n : ns, out_len = fwd ? ns : n;
+    if (log_enabled()) {
+        static const char* const names[] = {"left_inverse", "sqrt_adjoint", "sqrt", "adjoint"};
+        const bool tc = op == Op::LeftInverse && p->d.prec == ZL_MIXED && p->tc != nullptr && !p->force_plain;
+        log_call(names[(int)op], p, R, tc ? "tcgen05" : "cuda-core", tc && p->ytc != nullptr ? "tcgen05" : "cuda-core");
+    }
     const int chunk = p->d.max_rhs;
     for (int r0 = 0; r0 < R; r0 += chunk) {
         const int rc = std::min(chunk, R - r0);
@@ -219,6 +245,24 @@ zl_status run(zl_plan p, Op op, const void* in, void* out, int R, void* stream) 
 }  // namespace
 
 namespace zl {
+
+namespace {
+std::atomic<int> g_alloc_fail_in{0};   // 0: off; n > 0: the n-th allocation from now fails
+}
+
+cudaError_t dev_malloc(void** ptr, size_t bytes) {
+    int n = g_alloc_fail_in.load();
+    while (n > 0) {
+        if (g_alloc_fail_in.compare_exchange_weak(n, n - 1)) {
+            if (n == 1) {
+                *ptr = nullptr;
+                return cudaErrorMemoryAllocation;
+            }
+            break;
+        }
+    }
+    return cudaMalloc(ptr, bytes);
+}
 
 cudaEvent_t StageTimer::take() {
     if (!pool.empty()) {
@@ -261,6 +305,12 @@ StageTimer::~StageTimer() {
 }  // namespace zl
 
 extern "C" {
+
+zl_status zl_set_test_alloc_failure(int n) {
+    if (n < 0) return ZL_ERR_ARG;
+    zl::g_alloc_fail_in.store(n);
+    return ZL_OK;
+}
 
 zl_status zl_set_stage_timing(zl_plan p, int enable) {
     if (!valid_plan(p)) return ZL_ERR_ARG;
@@ -311,11 +361,11 @@ zl_status zl_gaussian_spectrum(int nx, int ny, double ell, double* out) {
     return ZL_OK;
 }
 
-zl_status zl_setup(const zl_desc* desc, const void* Z, const double* spectrum, void* stream, zl_plan* out) {
-    if (out == nullptr) return ZL_ERR_ARG;
-    *out = nullptr;
-    if (desc == nullptr || Z == nullptr || spectrum == nullptr) return ZL_ERR_ARG;
-    const zl_desc d = *desc;
+}  // extern "C"
+
+namespace {
+
+zl_status validate_desc(const zl_desc& d) {
     if (d.prec != ZL_FP64 && d.prec != ZL_FP32 && d.prec != ZL_MIXED) return ZL_ERR_ARG;
     if (!(d.tau >= 0.0) || !std::isfinite(d.tau)) return ZL_ERR_ARG;
     if (d.nx < 1 || d.ny < 1 || d.nw < 1 || d.K < 1 || d.max_rhs < 1 || d.max_rhs > 65535) return ZL_ERR_SHAPE;
@@ -323,75 +373,80 @@ zl_status zl_setup(const zl_desc* desc, const void* Z, const double* spectrum, v
     const long long nh = (long long)d.nx * d.ny;
     if (nh > (1LL << 30) || (long long)d.nw * d.K > 16384) return ZL_ERR_SHAPE;
     if (zl::setup_smem_bytes(d.nw, d.K) > 200 * 1024) return ZL_ERR_SHAPE;
-    double lmax = -INFINITY;
-    for (long long s = 0; s < nh; ++s) {
-        if (!std::isfinite(spectrum[s])) return ZL_ERR_ARG;
-        lmax = std::max(lmax, spectrum[s]);
-    }
-    if (!(lmax > 0.0)) return ZL_ERR_ARG;
+    return ZL_OK;
+}
 
+// The host part of a plan from its kept modes (ascending packed indices) and their
+// eigenvalues: sizes, kept x- and y-frequencies, shape limits.  No device work.
+zl_status make_plan(const zl_desc& d, std::vector<int> modes, std::vector<double> lamS, zl_plan_s** out) {
+    *out = nullptr;
+    if (modes.empty()) return ZL_ERR_SHAPE;   // tau >= 1: no eigenvalue exceeds tau * max, nothing to apply
     zl_plan_s* p = new (std::nothrow) zl_plan_s();
     if (!p) return ZL_ERR_ALLOC;
     p->d = d;
-    p->nh = nh;
+    p->nh = (long long)d.nx * d.ny;
     p->g = std::min(d.nw, d.K);
     p->esize = d.prec == ZL_FP64 ? sizeof(double) : sizeof(float);
-    std::vector<double> lamS;
-    for (long long s = 0; s < nh; ++s)
-        if (spectrum[s] > d.tau * lmax) {
-            p->modes.push_back((int)s);
-            lamS.push_back(spectrum[s]);
-        }
+    p->modes = std::move(modes);
+    p->lamS = std::move(lamS);
     p->L = (int)p->modes.size();
-    if (p->L == 0) {   // tau >= 1: no eigenvalue exceeds tau * max, so there is nothing to apply
-        delete p;
-        return ZL_ERR_SHAPE;
-    }
     std::vector<char> used(d.nx, 0);
     for (int s : p->modes) used[s % d.nx] = 1;
-    std::vector<int> xfreq;
     for (int q = 0; q < d.nx; ++q)
-        if (used[q]) xfreq.push_back(q);
-    p->Px = (int)xfreq.size();
-    p->xfreq = xfreq;
-    {
-        std::vector<char> yused(d.ny, 0);
-        for (int s2 : p->modes) yused[s2 / d.nx] = 1;
-        p->Py = 0;
-        for (char c : yused) p->Py += c;
-        p->pys = (p->Py + 15) / 16 * 16;
-    }
+        if (used[q]) p->xfreq.push_back(q);
+    p->Px = (int)p->xfreq.size();
+    std::vector<char> yused(d.ny, 0);
+    for (int s2 : p->modes) yused[s2 / d.nx] = 1;
+    p->Py = 0;
+    for (char c : yused) p->Py += c;
+    p->pys = (p->Py + 15) / 16 * 16;
     // forward y-pass keeps the L accumulators in shared memory
     if ((size_t)p->L * p->esize + (size_t)p->Px * p->esize > 96 * 1024 ||
         (size_t)d.K * (p->Px + 32) * p->esize > 160 * 1024) {
         delete p;
         return ZL_ERR_SHAPE;
     }
+    *out = p;
+    return ZL_OK;
+}
 
+// The device part: the plan's copy of Z (from the caller's device buffer, or a host
+// buffer), the tables, the pseudo-inverse P (formed by the setup kernel, or copied from a
+// host buffer of a saved plan, with its recorded rank status), the tensor-core operands
+// and the allocation-free entry point's preparation.  Frees the plan on any error except
+// ZL_ERR_RANK.
+zl_status finish_plan(zl_plan_s* p, const void* Z, bool Z_on_host, const void* P_host, int bad_column,
+                      cudaStream_t s, zl_plan* out) {
+    const zl_desc& d = p->d;
     if (cudaGetDevice(&p->device) != cudaSuccess) {
         delete p;
         return ZL_ERR_CUDA;
     }
-    cudaStream_t s = (cudaStream_t)stream;
-    const size_t mbytes = (size_t)d.K * d.nw * nh * p->esize;
+    const size_t mbytes = (size_t)d.K * d.nw * p->nh * p->esize;
     const size_t tbytes = (size_t)d.max_rhs * d.K * d.ny * p->Px * p->esize;
     cudaError_t e = cudaSuccess;
-    if (e == cudaSuccess) e = cudaMalloc(&p->Zc, mbytes);
-    if (e == cudaSuccess) e = cudaMalloc(&p->P, mbytes);
-    if (e == cudaSuccess) e = cudaMalloc(&p->t1, std::max<size_t>(tbytes, 16));
-    if (e == cudaSuccess) e = cudaMalloc((void**)&p->d_status, sizeof(int));
-    if (e == cudaSuccess) e = cudaMemcpyAsync(p->Zc, Z, mbytes, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = zl::dev_malloc((void**)&p->Zc, mbytes);
+    if (e == cudaSuccess) e = zl::dev_malloc((void**)&p->P, mbytes);
+    if (e == cudaSuccess) e = zl::dev_malloc((void**)&p->t1, std::max<size_t>(tbytes, 16));
+    if (e == cudaSuccess) e = zl::dev_malloc((void**)&p->d_status, sizeof(int));
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(p->Zc, Z, mbytes, Z_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s);
     if (e == cudaSuccess) {
         static const int kNone = INT_MAX;
         e = cudaMemcpyAsync(p->d_status, &kNone, sizeof(int), cudaMemcpyHostToDevice, s);
     }
     if (e == cudaSuccess) {
-        e = d.prec == ZL_FP64 ? build_tables<double>(*p, p->td, lamS, xfreq, s)
-                              : build_tables<float>(*p, p->tf, lamS, xfreq, s);
+        e = d.prec == ZL_FP64 ? build_tables<double>(*p, p->td, p->lamS, p->xfreq, s)
+                              : build_tables<float>(*p, p->tf, p->lamS, p->xfreq, s);
     }
-    if (e == cudaSuccess) e = zl::launch_setup_columns(d, nh, Z, p->P, p->d_status, s);
     int status = INT_MAX;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&status, p->d_status, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (P_host == nullptr) {
+        if (e == cudaSuccess) e = zl::launch_setup_columns(d, p->nh, Z_on_host ? p->Zc : Z, p->P, p->d_status, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&status, p->d_status, sizeof(int), cudaMemcpyDeviceToHost, s);
+    } else {
+        if (e == cudaSuccess) e = cudaMemcpyAsync(p->P, P_host, mbytes, cudaMemcpyHostToDevice, s);
+        if (bad_column >= 0) status = bad_column;
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
         free_plan(p);
@@ -418,6 +473,109 @@ zl_status zl_setup(const zl_desc* desc, const void* Z, const double* spectrum, v
         return ss;
     }
     *out = p;
+    return ZL_OK;
+}
+
+constexpr char kPlanMagic[8] = {'Z', 'L', 'P', 'L', 'A', 'N', '1', '\0'};
+
+}  // namespace
+
+extern "C" {
+
+zl_status zl_setup(const zl_desc* desc, const void* Z, const double* spectrum, void* stream, zl_plan* out) {
+    if (out == nullptr) return ZL_ERR_ARG;
+    *out = nullptr;
+    if (desc == nullptr || Z == nullptr || spectrum == nullptr) return ZL_ERR_ARG;
+    const zl_desc d = *desc;
+    const zl_status vs = validate_desc(d);
+    if (vs != ZL_OK) return vs;
+    const long long nh = (long long)d.nx * d.ny;
+    double lmax = -INFINITY;
+    for (long long s = 0; s < nh; ++s) {
+        if (!std::isfinite(spectrum[s])) return ZL_ERR_ARG;
+        lmax = std::max(lmax, spectrum[s]);
+    }
+    if (!(lmax > 0.0)) return ZL_ERR_ARG;
+    std::vector<int> modes;
+    std::vector<double> lamS;
+    for (long long s = 0; s < nh; ++s)
+        if (spectrum[s] > d.tau * lmax) {
+            modes.push_back((int)s);
+            lamS.push_back(spectrum[s]);
+        }
+    zl_plan_s* p = nullptr;
+    const zl_status ms = make_plan(d, std::move(modes), std::move(lamS), &p);
+    if (ms != ZL_OK) return ms;
+    return finish_plan(p, Z, false, nullptr, -1, (cudaStream_t)stream, out);
+}
+
+zl_status zl_plan_save(zl_plan p, const char* path) {
+    if (p == nullptr || p->P == nullptr || path == nullptr) return ZL_ERR_ARG;
+    const size_t mbytes = (size_t)p->d.K * p->d.nw * p->nh * p->esize;
+    std::vector<char> zc(mbytes), pc(mbytes);
+    if (cudaMemcpy(zc.data(), p->Zc, mbytes, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(pc.data(), p->P, mbytes, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return ZL_ERR_CUDA;
+    FILE* f = std::fopen(path, "wb");
+    if (f == nullptr) return ZL_ERR_ARG;
+    const int32_t L = p->L, bad = p->bad_column;
+    const uint64_t mb = mbytes;
+    bool ok = std::fwrite(kPlanMagic, 1, sizeof(kPlanMagic), f) == sizeof(kPlanMagic) &&
+              std::fwrite(&p->d, sizeof(zl_desc), 1, f) == 1 && std::fwrite(&L, sizeof(L), 1, f) == 1 &&
+              std::fwrite(&bad, sizeof(bad), 1, f) == 1 && std::fwrite(&mb, sizeof(mb), 1, f) == 1 &&
+              std::fwrite(p->modes.data(), sizeof(int), (size_t)L, f) == (size_t)L &&
+              std::fwrite(p->lamS.data(), sizeof(double), (size_t)L, f) == (size_t)L &&
+              std::fwrite(zc.data(), 1, mbytes, f) == mbytes && std::fwrite(pc.data(), 1, mbytes, f) == mbytes;
+    ok = (std::fclose(f) == 0) && ok;
+    return ok ? ZL_OK : ZL_ERR_ARG;
+}
+
+zl_status zl_plan_load(const char* path, void* stream, zl_plan* out) {
+    if (out == nullptr) return ZL_ERR_ARG;
+    *out = nullptr;
+    if (path == nullptr) return ZL_ERR_ARG;
+    FILE* f = std::fopen(path, "rb");
+    if (f == nullptr) return ZL_ERR_ARG;
+    char magic[sizeof(kPlanMagic)];
+    zl_desc d;
+    int32_t L = 0, bad = -1;
+    uint64_t mb = 0;
+    bool ok = std::fread(magic, 1, sizeof(magic), f) == sizeof(magic) &&
+              std::memcmp(magic, kPlanMagic, sizeof(magic)) == 0 && std::fread(&d, sizeof(d), 1, f) == 1 &&
+              std::fread(&L, sizeof(L), 1, f) == 1 && std::fread(&bad, sizeof(bad), 1, f) == 1 &&
+              std::fread(&mb, sizeof(mb), 1, f) == 1;
+    ok = ok && validate_desc(d) == ZL_OK;
+    const long long nh = ok ? (long long)d.nx * d.ny : 0;
+    const size_t esize = d.prec == ZL_FP64 ? sizeof(double) : sizeof(float);
+    ok = ok && L >= 1 && L <= nh && mb == (uint64_t)d.K * d.nw * nh * esize && bad >= -1 && bad < nh;
+    std::vector<int> modes;
+    std::vector<double> lamS;
+    std::vector<char> zc, pc;
+    if (ok) {
+        modes.resize(L);
+        lamS.resize(L);
+        ok = std::fread(modes.data(), sizeof(int), (size_t)L, f) == (size_t)L &&
+             std::fread(lamS.data(), sizeof(double), (size_t)L, f) == (size_t)L;
+    }
+    for (int i = 0; ok && i < L; ++i)   // ascending mode indices inside the grid, positive eigenvalues
+        ok = modes[i] >= 0 && modes[i] < nh && (i == 0 || modes[i] > modes[i - 1]) && lamS[i] > 0.0 &&
+             std::isfinite(lamS[i]);
+    if (ok) {
+        zc.resize(mb);
+        pc.resize(mb);
+        ok = std::fread(zc.data(), 1, mb, f) == mb && std::fread(pc.data(), 1, mb, f) == mb;
+    }
+    std::fclose(f);
+    if (!ok) return ZL_ERR_ARG;
+    zl_plan_s* p = nullptr;
+    const zl_status ms = make_plan(d, std::move(modes), std::move(lamS), &p);
+    if (ms != ZL_OK) return ms;
+    return finish_plan(p, zc.data(), true, pc.data(), bad, (cudaStream_t)stream, out);
+}
+
+zl_status zl_get_desc(zl_plan p, zl_desc* desc) {
+    if (!valid_plan(p) || desc == nullptr) return ZL_ERR_ARG;
+    *desc = p->d;
     return ZL_OK;
 }
 
@@ -484,8 +642,8 @@ static int host_piece(int max_rhs) {
 static cudaError_t host_staging(zl_plan_s* p, size_t in_b, size_t out_b) {
     if (p->h_x != nullptr) return cudaSuccess;
     const int piece = host_piece(p->d.max_rhs);
-    cudaError_t e = cudaMalloc(&p->h_x, 2 * piece * in_b);
-    if (e == cudaSuccess) e = cudaMalloc(&p->h_xt, 2 * piece * out_b);
+    cudaError_t e = zl::dev_malloc((void**)&p->h_x, 2 * piece * in_b);
+    if (e == cudaSuccess) e = zl::dev_malloc((void**)&p->h_xt, 2 * piece * out_b);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->h_in, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->h_out, cudaStreamNonBlocking);
     for (cudaEvent_t* ev : {&p->h_start, &p->h_in_done[0], &p->h_in_done[1], &p->h_comp_done[0], &p->h_comp_done[1],

@@ -122,7 +122,7 @@ zl_status autotune(zl_batch b, cudaStream_t s) {
     void *x = nullptr, *xt = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     zl_status st = ZL_OK;
-    if (cudaMalloc(&x, in_max) != cudaSuccess || cudaMalloc(&xt, out_max) != cudaSuccess) st = ZL_ERR_ALLOC;
+    if (zl::dev_malloc((void**)&x, in_max) != cudaSuccess || zl::dev_malloc((void**)&xt, out_max) != cudaSuccess) st = ZL_ERR_ALLOC;
     if (st == ZL_OK && (cudaMemsetAsync(x, 0, in_max, s) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
                         cudaEventCreate(&e1) != cudaSuccess))
         st = ZL_ERR_CUDA;

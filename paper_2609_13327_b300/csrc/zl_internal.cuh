@@ -63,6 +63,7 @@ struct zl_plan_s {
     int pys = 0;            // Py rounded up to 16 (row stride of the kept y-basis table)
     int bad_column = -1;
     std::vector<int> modes; // kept packed indices (host copy)
+    std::vector<double> lamS; // their eigenvalues
     std::vector<int> xfreq; // kept x-frequencies (packed x-index), in the order of the x-pass
     size_t esize = 0;       // element size of caller buffers (8 or 4)
 
@@ -97,6 +98,10 @@ struct zl_plan_s {
 };
 
 namespace zl {
+
+// Every device allocation of the library goes through dev_malloc, so that the test hook
+// zl_set_test_alloc_failure can make the n-th one fail as if the device were full.
+cudaError_t dev_malloc(void** ptr, size_t bytes);
 
 // k_setup.cu
 cudaError_t launch_setup_columns(const zl_desc& d, long long nh, const void* Z, void* P, int* d_status,

@@ -30,7 +30,8 @@ EXPORTS = ["zl_setup", "zl_get_info", "zl_get_modes", "zl_apply_left_inverse", "
            "zl_gaussian_spectrum", "zl_set_stage_timing", "zl_get_stage_times", "zl_get_runtime_info",
            "zl_apply_left_inverse_static", "zl_setup_batch", "zl_batch_get_info", "zl_apply_left_inverse_batch",
            "zl_destroy_batch", "zl_standardize_ensemble", "zl_set_test_wait_timeout", "zl_column_svd",
-           "zl_xi_indicators", "zl_delta", "zl_apply_left_inverse_rows", "zl_scale_modes"]
+           "zl_xi_indicators", "zl_delta", "zl_apply_left_inverse_rows", "zl_scale_modes",
+           "zl_set_test_alloc_failure", "zl_plan_save", "zl_plan_load", "zl_get_desc"]
 STAGES = {"fwd_column": 0, "fwd_ypass": 1, "inv_ypass": 2, "inv_column": 3}
 
 
@@ -63,6 +64,10 @@ _lib.zl_destroy_batch.argtypes = [_vp]
 _lib.zl_column_svd.argtypes = [_vp, _vp, _vp, _vp, _vp]
 _lib.zl_apply_left_inverse_rows.argtypes = [_vp, _int, _int, _vp, _vp, _int, _vp]
 _lib.zl_scale_modes.argtypes = [_vp, _vp, _vp, _int, _vp]
+_lib.zl_set_test_alloc_failure.argtypes = [_int]
+_lib.zl_plan_save.argtypes = [_vp, ctypes.c_char_p]
+_lib.zl_plan_load.argtypes = [ctypes.c_char_p, _vp, ctypes.POINTER(_vp)]
+_lib.zl_get_desc.argtypes = [_vp, ctypes.c_void_p]
 _lib.zl_xi_indicators.argtypes = [_vp, _int, _vp, _vp]
 _lib.zl_delta.argtypes = [_vp, _vp, _vp, _vp, _vp, _int, _vp]
 for _name in EXPORTS:
@@ -198,6 +203,31 @@ def zl_setup(Z, spectrum, tau=1e-10, prec="fp32", max_rhs=64, stream=None, nx=No
         raise err
     _check(code, "zl_setup")
     return Plan(h, d)
+
+
+def zl_plan_save(plan, path):
+    """Write the plan's descriptor, modes, Z copy and pseudo-inverse to `path`."""
+    _check(_lib.zl_plan_save(plan.handle, os.fsencode(path)), "zl_plan_save")
+
+
+def zl_plan_load(path, stream=None):
+    """Restore a plan saved by zl_plan_save (no per-column factorisation)."""
+    h = _vp()
+    code = _lib.zl_plan_load(os.fsencode(path), _stream_handle(stream), ctypes.byref(h))
+    if code == ZL_ERR_RANK:
+        plan = Plan(h, _desc_of(h))
+        err = ZLError(code, "zl_plan_load")
+        err.bad_column = plan.bad_column
+        plan.destroy()
+        raise err
+    _check(code, "zl_plan_load")
+    return Plan(h, _desc_of(h))
+
+
+def _desc_of(handle):
+    d = zl_desc()
+    _check(_lib.zl_get_desc(handle, ctypes.byref(d)), "zl_get_desc")
+    return d
 
 
 def _apply(fn, plan, inp, in_shape, out_shape, out, stream, where):

@@ -68,3 +68,16 @@ def test_reference_arm_under_torchrun_prints_from_rank_zero_only():
     assert r.returncode == 0, r.stderr[-2000:]
     lines = json_lines(r.stdout)
     assert len(lines) == 1 and lines[0]["impl"] == "reference"
+
+
+@pytest.mark.parametrize("ny,world", [(256, 1), (256, 3), (128, 8), (7, 3), (2, 4)])
+def test_slab_rows_cover_the_grid_once(ny, world):
+    """bench.py --partition slabs: the ranks' row ranges are disjoint, cover 0..ny-1 in order,
+    and differ in size by at most one row (a rank may get none when world > ny)."""
+    import bench
+    cuts = [bench.slab_rows(ny, world, r) for r in range(world)]
+    assert cuts[0][0] == 0 and cuts[-1][1] == ny
+    for (a0, a1), (b0, b1) in zip(cuts[:-1], cuts[1:]):
+        assert a1 == b0
+    sizes = [b - a for a, b in cuts]
+    assert max(sizes) - min(sizes) <= 1 and min(sizes) >= 0

@@ -68,11 +68,13 @@ def check_all_ops(zl, c, R=None):
     xt = synth.coefficients(w, c.plan.L, R=R, dtype=c.dt)
     xg, xtg = torch.from_numpy(x).cuda(), torch.from_numpy(xt).cuda()
     x64, xt64 = x.astype(np.float64), xt.astype(np.float64)
+    # every output buffer starts NaN-poisoned: an element a kernel fails to write fails the check
+    nan = lambda shape: torch.full(shape, float("nan"), dtype=xg.dtype, device="cuda")  # noqa: E731
     got = {
-        "left_inverse": zl.zl_apply_left_inverse(c.plan, xg),
-        "sqrt": zl.zl_apply_sqrt(c.plan, xtg),
-        "adjoint": zl.zl_apply_adjoint(c.plan, xtg),
-        "sqrt_adjoint": zl.zl_apply_sqrt_adjoint(c.plan, xg),
+        "left_inverse": zl.zl_apply_left_inverse(c.plan, xg, nan(xtg.shape)),
+        "sqrt": zl.zl_apply_sqrt(c.plan, xtg, nan(xg.shape)),
+        "adjoint": zl.zl_apply_adjoint(c.plan, xtg, nan(xg.shape)),
+        "sqrt_adjoint": zl.zl_apply_sqrt_adjoint(c.plan, xg, nan(xtg.shape)),
     }
     torch.cuda.synchronize()
     ref = {
