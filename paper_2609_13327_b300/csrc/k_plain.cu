@@ -195,6 +195,7 @@ inv_ypass(const T* __restrict__ c, const T* __restrict__ by, const int* __restri
     }
 }
 
+
 // ---------------------------------------------------------------------------
 // inverse, pass 2: inverse x-pass + per-column product,
 // CTA = (grid row y, column tile, rhs r); one thread per column
@@ -233,6 +234,112 @@ inv_xpass_column(const T* __restrict__ u, const T* __restrict__ M, const T* __re
         if (k < K) s0 = fma(M[((long long)k * nw + l) * nh + m], ys[(size_t)k * blockDim.x + threadIdx.x], s0);
         out[((long long)r * nw + l) * nh + m] = s0 + s1;
     }
+}
+
+
+// ---------------------------------------------------------------------------
+// inverse, pass 2, several right-hand sides per CTA: CTA = (grid row y, column tile,
+// RC right-hand sides), one thread per column.  Member by member, the thread forms
+// y_k = sum_jx b_jx(x) u[r][k][y][jx] for its RC right-hand sides (the basis column of
+// the thread and the u rows of the CTA staged in shared memory, u with the right-hand
+// sides innermost so that one vector load serves them all) and adds M[k][l][m] y_k to
+// NWM x RC register accumulators, so every element of M is read once per RC
+// right-hand sides instead of once per right-hand side.  NWM >= n_w.
+// ---------------------------------------------------------------------------
+template <typename T, int NWM, int RC>
+__global__ void __launch_bounds__(128)
+inv_xpass_column_rc(const T* __restrict__ u, const T* __restrict__ M, const T* __restrict__ bx, T* __restrict__ out,
+                    int R, int nw, int K, int nx, int ny, int Px) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* us = reinterpret_cast<T*>(smem_raw);            // [K][Px][RC]
+    T* bs = us + (size_t)K * Px * RC;                  // [Px][blockDim]
+    const int y = blockIdx.x, xt = blockIdx.y, r0 = blockIdx.z * RC;
+    const long long nh = (long long)nx * ny;
+    for (int e = threadIdx.x; e < K * Px * RC; e += blockDim.x) {
+        const int r = e % RC, kj = e / RC, k = kj / Px, jx = kj - k * Px;
+        us[e] = (r0 + r < R) ? u[(((long long)(r0 + r) * K + k) * ny + y) * Px + jx] : T(0);
+    }
+    const int xc = xt * blockDim.x + threadIdx.x;
+    for (int jx = 0; jx < Px; ++jx) bs[(size_t)jx * blockDim.x + threadIdx.x] = xc < nx ? bx[(size_t)jx * nx + xc] : T(0);
+    __syncthreads();
+    if (xc >= nx) return;
+    const long long m = (long long)y * nx + xc;
+    T acc[NWM][RC];
+#pragma unroll
+    for (int l = 0; l < NWM; ++l)
+#pragma unroll
+        for (int r = 0; r < RC; ++r) acc[l][r] = T(0);
+    const T* bcol = bs + threadIdx.x;
+    for (int k = 0; k < K; ++k) {
+        T yk[RC];
+#pragma unroll
+        for (int r = 0; r < RC; ++r) yk[r] = T(0);
+        const T* uk = us + (size_t)k * Px * RC;
+        for (int jx = 0; jx < Px; ++jx) {
+            const T b = bcol[(size_t)jx * blockDim.x];
+#pragma unroll
+            for (int r = 0; r < RC; ++r) yk[r] = fma(b, uk[jx * RC + r], yk[r]);
+        }
+#pragma unroll
+        for (int l = 0; l < NWM; ++l) {
+            if (l < nw) {
+                const T mv = M[((long long)k * nw + l) * nh + m];
+#pragma unroll
+                for (int r = 0; r < RC; ++r) acc[l][r] = fma(mv, yk[r], acc[l][r]);
+            }
+        }
+    }
+#pragma unroll
+    for (int l = 0; l < NWM; ++l)
+#pragma unroll
+        for (int r = 0; r < RC; ++r)
+            if (l < nw && r0 + r < R) out[((long long)(r0 + r) * nw + l) * nh + m] = acc[l][r];
+}
+
+template <typename T, int NWM, int RC>
+cudaError_t launch_inv_rc(const zl_plan_s& p, const T* u, const T* M, const T* bx, T* out, int R, cudaStream_t s) {
+    const int nx = p.d.nx, threads = 128;
+    const size_t smem = ((size_t)p.d.K * p.Px * RC + (size_t)p.Px * threads) * sizeof(T);
+    cudaError_t e = cudaFuncSetAttribute(inv_xpass_column_rc<T, NWM, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid(p.d.ny, (nx + threads - 1) / threads, (R + RC - 1) / RC);
+    inv_xpass_column_rc<T, NWM, RC><<<grid, threads, smem, s>>>(u, M, bx, out, R, p.d.nw, p.d.K, nx, p.d.ny, p.Px);
+    return cudaGetLastError();
+}
+
+// RC of the multi-rhs inverse column pass for this plan, or 0 when the one-rhs form runs:
+// n_w <= 64, its shared staging under 160 KB, at least two right-hand sides, and rows of at
+// least 64 columns (narrower rows would leave most of its 128-thread column tile idle).
+// RC keeps the NWM x RC accumulators at 128 registers per thread in FP32, 64 in FP64.
+template <typename T>
+int inv_multi_fits(const zl_plan_s& p, int R) {
+    const int nw = p.d.nw;
+    auto fits = [&](int rc) { return ((size_t)p.d.K * p.Px * rc + (size_t)p.Px * 128) * sizeof(T) <= 160 * 1024; };
+    if (R < 2 || p.d.nx < 64) return 0;
+    if (sizeof(T) == 4) {
+        if (nw <= 16 && fits(8)) return 8;
+        if (nw <= 32 && fits(4)) return 4;
+        if (nw <= 64 && fits(2)) return 2;
+    } else {
+        if (nw <= 16 && fits(4)) return 4;
+        if (nw <= 32 && fits(2)) return 2;
+    }
+    return 0;
+}
+
+template <typename T>
+cudaError_t launch_inv_multi(const zl_plan_s& p, const T* u, const T* M, const T* bx, T* out, int R, cudaStream_t s) {
+    const int rc = inv_multi_fits<T>(p, R);
+    if (sizeof(T) == 4) {
+        if (rc == 8) return launch_inv_rc<T, 16, 8>(p, u, M, bx, out, R, s);
+        if (rc == 4) return launch_inv_rc<T, 32, 4>(p, u, M, bx, out, R, s);
+        if (rc == 2) return launch_inv_rc<T, 64, 2>(p, u, M, bx, out, R, s);
+    } else {
+        if (rc == 4) return launch_inv_rc<T, 16, 4>(p, u, M, bx, out, R, s);
+        if (rc == 2) return launch_inv_rc<T, 32, 2>(p, u, M, bx, out, R, s);
+    }
+    return cudaErrorNotSupported;
 }
 
 // Right-hand sides per CTA of the forward column kernel: the plan's forced choice if it
@@ -606,6 +713,12 @@ cudaError_t inverse_plain(const zl_plan_s& p, const Tables<T>& t, const T* M, co
     inv_ypass<T><<<dim3(K, R), kThreads, smem, s>>>(c, t.by, t.m_py, t.grp_start, t.grp_modes, scale, u, K, ny, p.Px, p.L);
     p.timer.end(s);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (inv_multi_fits<T>(p, R) > 0) {
+        p.timer.begin(ZL_STAGE_INV_COLUMN, s);
+        e = launch_inv_multi<T>(p, u, M, t.bx, out, R, s);
+        p.timer.end(s);
+        return e;
+    }
     int threads = nx < kThreads ? ((nx + 31) / 32) * 32 : kThreads;
     while ((size_t)K * (p.Px + threads) * sizeof(T) > 160 * 1024 && threads > 32) threads /= 2;
     smem = (size_t)K * (p.Px + threads) * sizeof(T);
