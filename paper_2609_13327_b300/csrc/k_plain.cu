@@ -197,6 +197,79 @@ inv_ypass(const T* __restrict__ c, const T* __restrict__ by, const int* __restri
 
 
 // ---------------------------------------------------------------------------
+// inverse, pass 1 as a small dense GEMM per (member k, rhs r):
+//   u[r][k][y][jx] = sum_i byk[y][i] C[i][jx],  C[i][jx] = scale_j c[r][k][j] for the kept
+//   mode j = (i-th kept y-frequency, jx-th kept x-frequency), 0 for the others.
+// C is built in shared memory with its columns grouped as [i][jx % 4][jx / 4] so that a
+// thread's QJ x-frequencies (jx = g + 4 q, g = its group) are QJ consecutive words; the
+// kept y-basis is staged 64 rows at a time; thread (row yy, group g) accumulates its QJ
+// outputs with one basis load and QJ / 4 vector loads of C per kept y-frequency, and the
+// 64 x Px output tile leaves through shared memory with coalesced stores.
+// ---------------------------------------------------------------------------
+constexpr int kInvYRows = 64;
+
+template <typename T, int QJ>
+__global__ void __launch_bounds__(kThreads)
+inv_ypass_dense(const T* __restrict__ c, const T* __restrict__ byk, const int* __restrict__ m_ipy,
+                const int* __restrict__ m_jx, const T* __restrict__ scale, T* __restrict__ u, int K, int ny, int Px,
+                int L, int Py, int pys) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int CW = 4 * QJ;                           // C row width (x-frequency slots)
+    T* C = reinterpret_cast<T*>(smem_raw);               // [Py][4][QJ]
+    T* bys = C + (size_t)Py * CW;                        // [kInvYRows][Py + 1]
+    T* ot = bys + (size_t)kInvYRows * (Py + 1);          // [kInvYRows][Px]
+    const int k = blockIdx.x, r = blockIdx.y;
+    const T* src = c + ((long long)r * K + k) * L;
+    for (int e = threadIdx.x; e < Py * CW; e += blockDim.x) C[e] = T(0);
+    __syncthreads();
+    for (int j = threadIdx.x; j < L; j += blockDim.x) {
+        const int jx = m_jx[j];
+        C[(size_t)m_ipy[j] * CW + (jx & 3) * QJ + (jx >> 2)] = src[j] * scale[j];
+    }
+    const int yy = threadIdx.x % kInvYRows, g = threadIdx.x / kInvYRows;   // g = 0..3
+    T* dst = u + ((long long)r * K + k) * ny * Px;
+    for (int y0 = 0; y0 < ny; y0 += kInvYRows) {
+        const int yn = min(kInvYRows, ny - y0);
+        __syncthreads();                                  // C complete; previous tile written out
+        for (int e = threadIdx.x; e < yn * Py; e += blockDim.x) {
+            const int a = e / Py, i = e - a * Py;
+            bys[(size_t)a * (Py + 1) + i] = byk[(size_t)(y0 + a) * pys + i];
+        }
+        __syncthreads();
+        T acc[QJ];
+#pragma unroll
+        for (int q = 0; q < QJ; ++q) acc[q] = T(0);
+        if (yy < yn) {
+            const T* brow = bys + (size_t)yy * (Py + 1);
+            for (int i = 0; i < Py; ++i) {
+                const T b = brow[i];
+                const T* crow = C + (size_t)i * CW + g * QJ;
+#pragma unroll
+                for (int q = 0; q < QJ; ++q) acc[q] = fma(b, crow[q], acc[q]);
+            }
+#pragma unroll
+            for (int q = 0; q < QJ; ++q) {
+                const int jx = g + 4 * q;
+                if (jx < Px) ot[(size_t)yy * Px + jx] = acc[q];
+            }
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < yn * Px; e += blockDim.x) dst[(size_t)y0 * Px + e] = ot[e];
+    }
+}
+
+template <typename T, int QJ>
+cudaError_t launch_inv_ypass_dense(const zl_plan_s& p, const Tables<T>& t, const T* scale, const T* c, T* u, int R,
+                                   cudaStream_t s) {
+    const size_t smem = ((size_t)p.Py * 4 * QJ + (size_t)kInvYRows * (p.Py + 1) + (size_t)kInvYRows * p.Px) * sizeof(T);
+    cudaError_t e = cudaFuncSetAttribute(inv_ypass_dense<T, QJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    inv_ypass_dense<T, QJ><<<dim3(p.d.K, R), kThreads, smem, s>>>(c, t.byk, t.m_ipy, t.m_jx, scale, u, p.d.K, p.d.ny,
+                                                                   p.Px, p.L, p.Py, p.pys);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // inverse, pass 2: inverse x-pass + per-column product,
 // CTA = (grid row y, column tile, rhs r); one thread per column
 // ---------------------------------------------------------------------------
@@ -707,12 +780,25 @@ cudaError_t inverse_plain(const zl_plan_s& p, const Tables<T>& t, const T* M, co
     const int nx = p.d.nx, ny = p.d.ny, K = p.d.K;
     T* u = reinterpret_cast<T*>(p.t1);
     size_t smem = (size_t)p.L * sizeof(T);
-    cudaError_t e = cudaFuncSetAttribute(inv_ypass<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+    cudaError_t e;
     p.timer.begin(ZL_STAGE_INV_YPASS, s);
-    inv_ypass<T><<<dim3(K, R), kThreads, smem, s>>>(c, t.by, t.m_py, t.grp_start, t.grp_modes, scale, u, K, ny, p.Px, p.L);
+    // the dense form when the kept y-frequencies are few (the GEMM does Py / (L / Px) times
+    // the sparse form's multiply-adds, about 1.3 at the benchmark shapes)
+    if (p.Py <= 64 && p.Px <= 64) {
+        if (p.Px <= 16) e = launch_inv_ypass_dense<T, 4>(p, t, scale, c, u, R, s);
+        else if (p.Px <= 32) e = launch_inv_ypass_dense<T, 8>(p, t, scale, c, u, R, s);
+        else if (p.Px <= 48) e = launch_inv_ypass_dense<T, 12>(p, t, scale, c, u, R, s);
+        else e = launch_inv_ypass_dense<T, 16>(p, t, scale, c, u, R, s);
+    } else {
+        e = cudaFuncSetAttribute(inv_ypass<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess) {
+            inv_ypass<T><<<dim3(K, R), kThreads, smem, s>>>(c, t.by, t.m_py, t.grp_start, t.grp_modes, scale, u, K, ny,
+                                                            p.Px, p.L);
+            e = cudaGetLastError();
+        }
+    }
     p.timer.end(s);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (e != cudaSuccess) return e;
     if (inv_multi_fits<T>(p, R) > 0) {
         p.timer.begin(ZL_STAGE_INV_COLUMN, s);
         e = launch_inv_multi<T>(p, u, M, t.bx, out, R, s);
