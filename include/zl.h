@@ -126,9 +126,11 @@ zl_status zl_get_desc(zl_plan plan, zl_desc* desc);
  *                     8, nw <= 32, K <= 64, at most 48 kept x-frequencies,
  *                     and not switched to the CUDA-core kernels by the batch
  *                     autotuner), 0 if it runs the CUDA-core kernels.
- *   device_error      0, or the code the tensor-core kernel recorded when one
- *                     of its bounded waits timed out (the call then returns
- *                     ZL_ERR_TIMEOUT).  Reading it synchronises the device.
+ *   device_error      0, or the code a TMA-fed kernel recorded when one of its
+ *                     bounded waits timed out (the call then returns
+ *                     ZL_ERR_TIMEOUT): 1-15 the tensor-core column kernel,
+ *                     17-31 the tensor-core y-pass, 33-34 the FP32 column
+ *                     kernel.  Reading it synchronises the device.
  *                     The code stays recorded until zl_set_test_wait_timeout
  *                     (plan, 0) clears it; the results of the applies queued
  *                     since the timeout are undefined.
@@ -138,14 +140,18 @@ zl_status zl_get_runtime_info(zl_plan plan, int* tensor_core_path, int* device_e
 /*
  * zl_set_test_wait_timeout -- a test hook of the failure-detection path; the
  * paper has no counterpart.  enable = 1: from the next apply on, the
- * tensor-core kernel's image producer issues no copies, so the MMA thread's
- * bounded wait for the first image runs out (about 2 s), the kernel records a
- * nonzero device error, frees its TMEM and returns; the results of such an
- * apply are undefined and zl_get_runtime_info reports ZL_ERR_TIMEOUT.
- * enable = 0: restores normal operation and clears the recorded device error.
- * No GPU fault is involved and the context stays usable.  The call
- * synchronises the device.  Errors: ZL_ERR_ARG (invalid plan, enable not 0 or
- * 1), ZL_ERR_UNSUPPORTED (the plan has no tensor-core path), ZL_ERR_CUDA.
+ * copy-issuing thread of the plan's TMA-fed left-inverse kernel (the
+ * tensor-core kernel's image producer, or the FP32 column kernel's stage
+ * producer) issues no copies, so the first bounded wait for a copy runs out
+ * (about 2 s), the kernel records a nonzero device error (the tensor-core
+ * kernel frees its TMEM) and returns; the results of such an apply are
+ * undefined and zl_get_runtime_info reports ZL_ERR_TIMEOUT.  enable = 0:
+ * restores normal operation and clears the recorded device error.  No GPU
+ * fault is involved and the context stays usable.  The call synchronises the
+ * device.  Errors: ZL_ERR_ARG (invalid plan, enable not 0 or 1),
+ * ZL_ERR_UNSUPPORTED (the plan's left inverse runs neither TMA-fed kernel:
+ * FP64 plans, or FP32 data with n_x not a multiple of 4, more than 64 kept
+ * x-frequencies or max_rhs < 4), ZL_ERR_CUDA.
  */
 zl_status zl_set_test_wait_timeout(zl_plan plan, int enable);
 
@@ -422,8 +428,9 @@ typedef struct zl_batch_s* zl_batch;   /* opaque; owned by libzl, freed by zl_de
  * from descs[i], Z[i], spectra[i]; same layouts, precisions and errors), then
  * an autotuner picks each instance's kernel variant by timing, on the
  * instance's own shape with max_rhs right-hand sides, the variants that meet
- * the plan's accuracy: the tcgen05 path (ZL_MIXED plans it supports) and the
- * CUDA-core path with 8, 4, 2 or 1 right-hand sides per CTA.  Choices are
+ * the plan's accuracy: the tcgen05 path (ZL_MIXED plans it supports), the
+ * register-tiled FP32 CUDA-core column kernel, and the per-column CUDA-core
+ * kernel with 8, 4, 2 or 1 right-hand sides per CTA.  Choices are
  * cached per shape for the process and, if the environment variable
  * ZL_AUTOTUNE_CACHE names a file, appended to and read from that file.
  * Setup synchronises `stream` and allocates (per-plan memory plus temporary
@@ -443,8 +450,11 @@ zl_status zl_setup_batch(int n, const zl_desc* descs, const void* const* Z, cons
  * zl_batch_get_info -- the plan of instance i (owned by the batch: query it
  * with zl_get_info / zl_get_modes / zl_get_runtime_info, apply it alone with
  * the single-plan entry points, never zl_destroy it) and the autotuned variant
- * (0 = tcgen05 or the default heuristic, 1..4 = CUDA-core with 8, 4, 2, 1
- * right-hand sides per CTA).  Either output may be NULL.
+ * (0 = the default heuristic: tcgen05 for the ZL_MIXED plans it supports, else
+ * the register-tiled FP32 column kernel where its tile fits; 1..4 = the
+ * per-column CUDA-core kernel with 8, 4, 2, 1 right-hand sides per CTA; 5 = a
+ * ZL_MIXED plan on the CUDA-core FP32 path with the default heuristic).  Either
+ * output may be NULL.
  */
 zl_status zl_batch_get_info(zl_batch batch, int i, zl_plan* plan, int* variant);
 

@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libzl.so")
-SOURCES = ["zl_api.cu", "k_setup.cu", "k_plain.cu", "k_tc.cu", "zl_static.cu", "zl_batch.cu", "zl_ensemble.cu", "k_diag.cu", "k_ytc.cu"]
+SOURCES = ["zl_api.cu", "k_setup.cu", "k_plain.cu", "k_tc.cu", "zl_static.cu", "zl_batch.cu", "zl_ensemble.cu", "k_diag.cu", "k_ytc.cu", "k_f32.cu"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

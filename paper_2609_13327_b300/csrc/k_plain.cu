@@ -21,6 +21,8 @@
 
 #include "zl_internal.cuh"
 
+#include <algorithm>
+
 namespace zl {
 
 namespace {
@@ -381,6 +383,157 @@ cudaError_t launch_inv_rc(const zl_plan_s& p, const T* u, const T* M, const T* b
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// inverse, pass 2, FP32 register-tiled form: CTA = (RC rhs, grid row y, 64-column chunk),
+// looping over member chunks of KC = 128 / RC members, so that a chunk holds 128
+// (rhs, member) rows:
+//   phase 1 (x-pass): Y[(r, k)][x] = sum_jx u[r][k][y][jx] bx[jx][x], a GEMM with thread
+//     tiles of 8 rows x 4 columns over 128-bit shared loads of the transposed u tile and
+//     of the basis (lanes: 4 row groups x 8 column groups, warps: 4 x 2);
+//   phase 2 (per-column product): out[r][l][x] += sum_k M[k][l][x] Y[(r, k)][x], thread =
+//     (column, quarter of the levels) with its RC x NLQ sums in registers across the
+//     member chunks; each member-matrix element is read once per CTA.
+// CTAs of the same row and column chunk (different rhs) are adjacent, so the
+// member-matrix tile they share is read from L2.
+// ---------------------------------------------------------------------------
+constexpr int kIvXC = 64;                // grid columns per CTA
+constexpr int kIvLdY = kIvXC + 4;        // row stride of Y and of the basis tile
+constexpr int kIvLdU = 128 + 4;          // row stride of the transposed u tile
+
+inline size_t inv_sgemm_smem(int Px) {
+    return ((size_t)128 * kIvLdY + (size_t)Px * kIvLdU + (size_t)Px * kIvLdY) * sizeof(float);
+}
+
+template <int RC>
+__global__ void __launch_bounds__(kThreads, 2)
+inv_column_sgemm(const float* __restrict__ u, const float* __restrict__ M, const float* __restrict__ bx,
+                 float* __restrict__ out, int R, int nw, int K, int nx, int ny, int Px) {
+    constexpr int KC = 128 / RC;
+    constexpr int NLQ = 32 / RC;                       // levels per thread in phase 2
+    constexpr int KU = NLQ >= 16 ? 1 : 16 / NLQ;       // members per phase-2 step (KU divides KC)
+    extern __shared__ float4 smem_f4[];
+    float* Ys = reinterpret_cast<float*>(smem_f4);     // [128][kIvLdY], row = r * KC + k
+    float* Ut = Ys + 128 * kIvLdY;                     // [Px][kIvLdU]
+    float* Bs = Ut + (size_t)Px * kIvLdU;              // [Px][kIvLdY]
+    const int tid = threadIdx.x;
+    const int r0 = blockIdx.x * RC, y = blockIdx.y, x0 = blockIdx.z * kIvXC;
+    const int xn = min(kIvXC, nx - x0);
+    const long long nh = (long long)nx * ny;
+    const int lane = tid & 31, warp = tid >> 5;
+    for (int j = warp; j < Px; j += kThreads / 32)
+        for (int xc = lane; xc < kIvXC; xc += 32) Bs[j * kIvLdY + xc] = xc < xn ? bx[(size_t)j * nx + x0 + xc] : 0.f;
+    const int rg = (warp & 3) * 4 + (lane & 3);        // rows 4 rg + i and 64 + 4 rg + i (i < 4)
+    const int cg = (warp >> 2) * 8 + (lane >> 2);      // columns 4 cg + j (j < 4)
+    const int xc2 = tid & (kIvXC - 1);                 // phase 2: column
+    const int l0 = (tid / kIvXC) * NLQ;                // phase 2: first level
+    const bool col_ok = xc2 < xn;
+    const long long m = (long long)y * nx + x0 + xc2;
+
+    float acc[RC][NLQ];
+#pragma unroll
+    for (int r = 0; r < RC; ++r)
+#pragma unroll
+        for (int i = 0; i < NLQ; ++i) acc[r][i] = 0.f;
+
+    for (int k0 = 0; k0 < K; k0 += KC) {
+        __syncthreads();                               // the previous chunk's phase 2 is done with Ys
+        for (int row = warp; row < 128; row += kThreads / 32) {
+            const int r = row / KC, k = row - r * KC;
+            const bool ok = r0 + r < R && k0 + k < K;
+            const float* src = u + (((long long)(r0 + r) * K + k0 + k) * ny + y) * Px;
+            for (int jx = lane; jx < Px; jx += 32) Ut[jx * kIvLdU + row] = ok ? src[jx] : 0.f;
+        }
+        __syncthreads();
+        float c[8][4];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) c[i][j] = 0.f;
+        for (int jx = 0; jx < Px; ++jx) {
+            const float4 ua = *reinterpret_cast<const float4*>(Ut + jx * kIvLdU + 4 * rg);
+            const float4 ub = *reinterpret_cast<const float4*>(Ut + jx * kIvLdU + 64 + 4 * rg);
+            const float4 bv = *reinterpret_cast<const float4*>(Bs + jx * kIvLdY + 4 * cg);
+            const float uu[8] = {ua.x, ua.y, ua.z, ua.w, ub.x, ub.y, ub.z, ub.w};
+            const float bb[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) c[i][j] = fmaf(uu[i], bb[j], c[i][j]);
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int row = (i < 4 ? 0 : 64) + 4 * rg + (i & 3);
+            *reinterpret_cast<float4*>(Ys + row * kIvLdY + 4 * cg) = make_float4(c[i][0], c[i][1], c[i][2], c[i][3]);
+        }
+        __syncthreads();
+        if (col_ok) {
+            // KU members per step with all their member-matrix loads issued first; members
+            // past K and levels past n_w are clamped to valid rows (their Y rows are zero,
+            // their sums are never stored)
+            const int kn = min(KC, K - k0);
+            const float* Mm = M + m;
+            const unsigned nhu = (unsigned)nh;
+            for (int kk = 0; kk < kn; kk += KU) {
+                float mv[KU][NLQ];
+#pragma unroll
+                for (int h = 0; h < KU; ++h)
+#pragma unroll
+                    for (int i = 0; i < NLQ; ++i)
+                        mv[h][i] = __ldg(Mm + ((unsigned)min(k0 + kk + h, K - 1) * (unsigned)nw +
+                                               (unsigned)min(l0 + i, nw - 1)) * nhu);
+#pragma unroll
+                for (int h = 0; h < KU; ++h) {
+                    float yv[RC];
+#pragma unroll
+                    for (int r = 0; r < RC; ++r) yv[r] = Ys[(r * KC + kk + h) * kIvLdY + xc2];
+#pragma unroll
+                    for (int i = 0; i < NLQ; ++i)
+#pragma unroll
+                        for (int r = 0; r < RC; ++r) acc[r][i] = fmaf(mv[h][i], yv[r], acc[r][i]);
+                }
+            }
+        }
+    }
+    if (!col_ok) return;
+#pragma unroll
+    for (int r = 0; r < RC; ++r)
+#pragma unroll
+        for (int i = 0; i < NLQ; ++i)
+            if (r0 + r < R && l0 + i < nw) out[((long long)(r0 + r) * nw + l0 + i) * nh + m] = acc[r][i];
+}
+
+template <int RC>
+cudaError_t launch_inv_sgemm(const zl_plan_s& p, const float* u, const float* M, const float* bx, float* out, int R,
+                             cudaStream_t s) {
+    const size_t smem = inv_sgemm_smem(p.Px);
+    cudaError_t e = cudaFuncSetAttribute(inv_column_sgemm<RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((R + RC - 1) / RC, p.d.ny, (p.d.nx + kIvXC - 1) / kIvXC);
+    inv_column_sgemm<RC><<<grid, kThreads, smem, s>>>(u, M, bx, out, R, p.d.nw, p.d.K, p.d.nx, p.d.ny, p.Px);
+    return cudaGetLastError();
+}
+
+// rhs per CTA of the register-tiled inverse column pass, or 0 when it does not apply
+// (P_x > 64 or n_w > 128): the largest of 8/4/2/1 whose phase-2 tile covers n_w levels
+// (4 x 32 / RC) and that does not exceed R.
+inline int inv_sgemm_rc(const zl_plan_s& p, int R) {
+    if (p.Px > 64 || p.d.nw > 128) return 0;
+    if ((unsigned long long)p.d.K * (unsigned long long)p.d.nw * (unsigned long long)p.nh >= (1ull << 32)) return 0;
+    int rc = p.d.nw <= 16 ? 8 : p.d.nw <= 32 ? 4 : p.d.nw <= 64 ? 2 : 1;
+    while (rc > 1 && rc > R) rc /= 2;
+    return rc;
+}
+
+cudaError_t launch_inv_sgemm_any(const zl_plan_s& p, const float* u, const float* M, const float* bx, float* out,
+                                 int R, cudaStream_t s) {
+    switch (inv_sgemm_rc(p, R)) {
+        case 8: return launch_inv_sgemm<8>(p, u, M, bx, out, R, s);
+        case 4: return launch_inv_sgemm<4>(p, u, M, bx, out, R, s);
+        case 2: return launch_inv_sgemm<2>(p, u, M, bx, out, R, s);
+        default: return launch_inv_sgemm<1>(p, u, M, bx, out, R, s);
+    }
+}
+
 // RC of the multi-rhs inverse column pass for this plan, or 0 when the one-rhs form runs:
 // n_w <= 64, its shared staging under 160 KB, at least two right-hand sides, and rows of at
 // least 64 columns (narrower rows would leave most of its 128-thread column tile idle).
@@ -440,6 +593,14 @@ cudaError_t launch_fwd_rc(const zl_plan_s& p, const T* x, const T* M, const T* b
 template <typename T>
 cudaError_t launch_fwd(const zl_plan_s& p, const T* x, const T* M, const T* bx, T* t1, int R, cudaStream_t s,
                        Rows rows) {
+    if constexpr (sizeof(T) == 4) {
+        // the TMA-fed FP32 kernel where it applies; a tensor map it cannot encode (an
+        // unaligned caller buffer) falls back to the per-column kernel
+        if (f32_column_supported(p, R)) {
+            const cudaError_t e = forward_column_f32(p, x, M, bx, t1, R, s, rows);
+            if (e != cudaErrorNotSupported) return e;
+        }
+    }
     switch (pick_rc(p, R, (size_t)KC * (p.d.nx + 1) * sizeof(T))) {
         case 8: return launch_fwd_rc<T, 8>(p, x, M, bx, t1, R, s, rows);
         case 4: return launch_fwd_rc<T, 4>(p, x, M, bx, t1, R, s, rows);
@@ -520,6 +681,107 @@ fwd_ypass_gemm(const T* __restrict__ t1, const T* __restrict__ byk, const int* _
             out[pr * L + j] = scale ? v * scale[j] : v;
         }
     }
+}
+
+// FP32 y-pass as one register-tiled GEMM over all pairs:
+//   D[i][n] = sum_y byk[y][i] t1[y][n],   n = pair * Px + jx (the flattened t1 row),
+// then x~[pair][j] = scale_j D[ipy_j][pair * Px + jx_j].  A CTA owns 64 consecutive
+// columns n (a pair may straddle two CTAs; each writes the modes whose column it holds)
+// and all kept y-frequencies: thread = (column, group of PYG y-frequencies), the column's
+// t1 value and a broadcast 128-bit basis load per 4 products.  The t1 and basis rows of
+// the next 32 values of y are loaded into registers while the current ones are used.
+constexpr int kYsN = 64;                 // columns per CTA
+constexpr int kYsY = 32;                 // rows of y per chunk
+
+template <int PYG>
+__global__ void __launch_bounds__(kThreads)
+fwd_ypass_sgemm(const float* __restrict__ t1, const float* __restrict__ byk, const int* __restrict__ m_ipy,
+                const int* __restrict__ m_jx, const float* __restrict__ scale, float* __restrict__ out, int npairs,
+                int ny, int Px, int L, int pys) {
+    constexpr int IG = kThreads / kYsN;
+    constexpr int PYT = IG * PYG;                  // kept y-frequencies covered (>= Py)
+    constexpr int TQ = kYsY * kYsN / kThreads;     // t1 values per thread per chunk
+    constexpr int BQ = (kYsY * PYT + kThreads - 1) / kThreads;
+    static_assert(PYG % 4 == 0, "128-bit basis loads");
+    __shared__ float Ts[kYsY][kYsN];
+    __shared__ __align__(16) float Bs[kYsY][PYT];
+    __shared__ float Ds[PYT][kYsN + 1];
+    const int tid = threadIdx.x;
+    const int n = tid % kYsN, g = tid / kYsN;
+    const long long ncols = (long long)npairs * Px;
+    const long long n0 = (long long)blockIdx.x * kYsN;
+
+    float tr[TQ], br[BQ];
+    auto fetch = [&](int y0) {
+#pragma unroll
+        for (int q = 0; q < TQ; ++q) {
+            const int e = tid + q * kThreads, row = e / kYsN, col = e % kYsN;
+            tr[q] = (y0 + row < ny && n0 + col < ncols) ? t1[(long long)(y0 + row) * ncols + n0 + col] : 0.f;
+        }
+#pragma unroll
+        for (int q = 0; q < BQ; ++q) {
+            const int e = tid + q * kThreads, row = e / PYT, i = e % PYT;
+            br[q] = (e < kYsY * PYT && y0 + row < ny && i < pys) ? byk[(long long)(y0 + row) * pys + i] : 0.f;
+        }
+    };
+    float acc[PYG];
+#pragma unroll
+    for (int i = 0; i < PYG; ++i) acc[i] = 0.f;
+    fetch(0);
+    for (int y0 = 0; y0 < ny; y0 += kYsY) {
+        __syncthreads();                               // the previous chunk has been used
+#pragma unroll
+        for (int q = 0; q < TQ; ++q) {
+            const int e = tid + q * kThreads;
+            Ts[e / kYsN][e % kYsN] = tr[q];
+        }
+#pragma unroll
+        for (int q = 0; q < BQ; ++q) {
+            const int e = tid + q * kThreads;
+            if (e < kYsY * PYT) Bs[e / PYT][e % PYT] = br[q];
+        }
+        __syncthreads();
+        if (y0 + kYsY < ny) fetch(y0 + kYsY);
+#pragma unroll 4
+        for (int yy = 0; yy < kYsY; ++yy) {
+            const float t = Ts[yy][n];
+            const float4* b = reinterpret_cast<const float4*>(&Bs[yy][g * PYG]);
+#pragma unroll
+            for (int q = 0; q < PYG / 4; ++q) {
+                const float4 bv = b[q];
+                acc[4 * q] = fmaf(bv.x, t, acc[4 * q]);
+                acc[4 * q + 1] = fmaf(bv.y, t, acc[4 * q + 1]);
+                acc[4 * q + 2] = fmaf(bv.z, t, acc[4 * q + 2]);
+                acc[4 * q + 3] = fmaf(bv.w, t, acc[4 * q + 3]);
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < PYG; ++i) Ds[g * PYG + i][n] = acc[i];
+    __syncthreads();
+    const long long p_lo = n0 / Px;
+    const long long p_hi = min((long long)npairs - 1, (n0 + kYsN - 1) / Px);
+    for (long long pr = p_lo; pr <= p_hi; ++pr) {
+        const long long c0 = pr * Px - n0;             // column of the pair's x-frequency 0
+        for (int j = tid; j < L; j += kThreads) {
+            const long long col = c0 + m_jx[j];
+            if (col < 0 || col >= kYsN) continue;
+            const float v = Ds[m_ipy[j]][col];
+            out[pr * L + j] = scale ? v * scale[j] : v;
+        }
+    }
+}
+
+template <int PYG>
+cudaError_t launch_ypass_sgemm(const zl_plan_s& p, const float* t1, const float* byk, const int* m_ipy,
+                               const int* m_jx, const float* scale, float* out, int R, cudaStream_t s, Rows rows) {
+    const long long npairs = (long long)R * p.d.K;
+    const long long grid = (npairs * p.Px + kYsN - 1) / kYsN;
+    p.timer.begin(ZL_STAGE_FWD_YPASS, s);
+    fwd_ypass_sgemm<PYG><<<(unsigned)grid, kThreads, 0, s>>>(t1, byk + (size_t)rows.y0 * p.pys, m_ipy, m_jx, scale,
+                                                             out, (int)npairs, rows.ny, p.Px, p.L, p.pys);
+    p.timer.end(s);
+    return cudaGetLastError();
 }
 
 // FP32 y-pass with the t1 rows of the CTA's pairs and the kept y-basis rows streamed
@@ -761,6 +1023,15 @@ cudaError_t forward_ypass_f32(const zl_plan_s& p, const float* t1, int ldp, cons
     return launch_ypass<float>(p, t1, ldp, p.tf.by, p.tf.m_py, p.tf.m_jx, scale, out, R, s, &p.tf, rows);
 }
 
+// the register-tiled FP32 y-pass over t1 rows of P_x values (the CUDA-core left inverse)
+cudaError_t launch_ypass_f32_sgemm(const zl_plan_s& p, const float* t1, const Tables<float>& t, const float* scale,
+                                   float* out, int R, cudaStream_t s, Rows rows) {
+    if (p.Py <= 16) return launch_ypass_sgemm<4>(p, t1, t.byk, t.m_ipy, t.m_jx, scale, out, R, s, rows);
+    if (p.Py <= 32) return launch_ypass_sgemm<8>(p, t1, t.byk, t.m_ipy, t.m_jx, scale, out, R, s, rows);
+    if (p.Py <= 48) return launch_ypass_sgemm<12>(p, t1, t.byk, t.m_ipy, t.m_jx, scale, out, R, s, rows);
+    return launch_ypass_sgemm<16>(p, t1, t.byk, t.m_ipy, t.m_jx, scale, out, R, s, rows);
+}
+
 template <typename T>
 cudaError_t forward_plain(const zl_plan_s& p, const Tables<T>& t, const T* M, const T* scale, const T* x, T* out,
                           int R, cudaStream_t s, Rows rows) {
@@ -771,6 +1042,9 @@ cudaError_t forward_plain(const zl_plan_s& p, const Tables<T>& t, const T* M, co
     p.timer.end(s);
     if (e != cudaSuccess) return e;
 
+    if constexpr (sizeof(T) == 4) {
+        if (p.Py <= 64) return launch_ypass_f32_sgemm(p, t1, t, scale, out, R, s, rows);
+    }
     return launch_ypass<T>(p, t1, p.Px, t.by, t.m_py, t.m_jx, scale, out, R, s, &t, rows);
 }
 
@@ -799,6 +1073,14 @@ cudaError_t inverse_plain(const zl_plan_s& p, const Tables<T>& t, const T* M, co
     }
     p.timer.end(s);
     if (e != cudaSuccess) return e;
+    if constexpr (sizeof(T) == 4) {
+        if (inv_sgemm_rc(p, R) > 0) {
+            p.timer.begin(ZL_STAGE_INV_COLUMN, s);
+            e = launch_inv_sgemm_any(p, u, M, t.bx, out, R, s);
+            p.timer.end(s);
+            return e;
+        }
+    }
     if (inv_multi_fits<T>(p, R) > 0) {
         p.timer.begin(ZL_STAGE_INV_COLUMN, s);
         e = launch_inv_multi<T>(p, u, M, t.bx, out, R, s);

@@ -722,14 +722,28 @@ void tc_release(zl_plan_s& p) {
 int tc_t1_stride(const zl_plan_s& p) { return p.tc ? p.tc->pxp : p.Px; }
 
 cudaError_t tc_clear_error(const zl_plan_s& p) {
+    if (p.d_werr) {
+        const cudaError_t e = cudaMemset(p.d_werr, 0, sizeof(int));
+        if (e != cudaSuccess) return e;
+    }
     if (!p.tc) return cudaSuccess;
     const cudaError_t e = cudaMemset(p.tc->d_err, 0, sizeof(int));
     return e != cudaSuccess ? e : ytc_clear_error(p);
 }
 
-// The column kernel's code, else the y-pass's (plus 16: codes of the tensor-core y-pass).
+// The code of the TMA-fed FP32 column kernel (plus 32), else the tensor-core column
+// kernel's, else the tensor-core y-pass's (plus 16).
 cudaError_t tc_read_error(const zl_plan_s& p, int* code) {
     *code = 0;
+    if (p.d_werr) {
+        int w = 0;
+        const cudaError_t e = cudaMemcpy(&w, p.d_werr, sizeof(int), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return e;
+        if (w != 0) {
+            *code = 32 + w;
+            return cudaSuccess;
+        }
+    }
     if (!p.tc) return cudaSuccess;
     cudaError_t e = cudaMemcpy(code, p.tc->d_err, sizeof(int), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess || *code != 0) return e;

@@ -164,6 +164,7 @@ void free_plan(zl_plan_s* p) {
     cudaFree(p->t1);
     release_host_staging(p);
     cudaFree(p->d_status);
+    cudaFree(p->d_werr);
     free_tables(p->td);
     free_tables(p->tf);
     delete p;
@@ -429,6 +430,8 @@ zl_status finish_plan(zl_plan_s* p, const void* Z, bool Z_on_host, const void* P
     if (e == cudaSuccess) e = zl::dev_malloc((void**)&p->P, mbytes);
     if (e == cudaSuccess) e = zl::dev_malloc((void**)&p->t1, std::max<size_t>(tbytes, 16));
     if (e == cudaSuccess) e = zl::dev_malloc((void**)&p->d_status, sizeof(int));
+    if (e == cudaSuccess) e = zl::dev_malloc((void**)&p->d_werr, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->d_werr, 0, sizeof(int), s);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(p->Zc, Z, mbytes, Z_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s);
     if (e == cudaSuccess) {
@@ -603,7 +606,8 @@ zl_status zl_get_runtime_info(zl_plan p, int* tensor_core_path, int* device_erro
 
 zl_status zl_set_test_wait_timeout(zl_plan p, int enable) {
     if (!valid_plan(p) || (enable != 0 && enable != 1)) return ZL_ERR_ARG;
-    if (p->tc == nullptr) return ZL_ERR_UNSUPPORTED;
+    if (p->tc == nullptr && !(p->d.prec != ZL_FP64 && zl::f32_column_supported(*p, p->d.max_rhs)))
+        return ZL_ERR_UNSUPPORTED;
     if (cudaDeviceSynchronize() != cudaSuccess) return ZL_ERR_CUDA;
     p->test_wait_timeout = enable;
     if (!enable && zl::tc_clear_error(*p) != cudaSuccess) return ZL_ERR_CUDA;

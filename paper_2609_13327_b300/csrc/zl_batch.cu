@@ -47,9 +47,12 @@ namespace {
 constexpr int kMaxGraphs = 4;
 constexpr int kTuneReps = 3;
 
-// variant v: 0 = default heuristics (tcgen05 for supported mixed plans), 1..4 = CUDA-core
-// path with 8, 4, 2, 1 right-hand sides per CTA
-const int kRcOf[5] = {0, 8, 4, 2, 1};
+// variant v: 0 = default heuristics (tcgen05 for supported mixed plans, else the
+// register-tiled FP32 column kernel where its tile fits), 1..4 = CUDA-core path with 8, 4,
+// 2, 1 right-hand sides per CTA of the per-column kernel, 5 = CUDA-core path with the
+// default heuristics (for a mixed plan: the register-tiled FP32 kernel instead of tcgen05)
+constexpr int kVariants = 6;
+const int kRcOf[kVariants] = {0, 8, 4, 2, 1, 0};
 
 void apply_variant(zl_plan p, int v) {
     p->force_plain = v != 0;
@@ -135,8 +138,9 @@ zl_status autotune(zl_batch b, cudaStream_t s) {
             best = it->second;
         } else {
             float tbest = -1.f;
-            for (int v = 0; v <= 4; ++v) {
-                if (v == 0 && p->d.prec == ZL_MIXED && p->tc == nullptr) continue;   // same as a CUDA-core variant
+            for (int v = 0; v < kVariants; ++v) {
+                if (v == 0 && p->d.prec == ZL_MIXED && p->tc == nullptr) continue;   // same as variant 5
+                if (v == 5 && p->d.prec != ZL_MIXED) continue;                       // same as variant 0
                 const float t = time_variant(p, v, x, xt, p->d.max_rhs, s, e0, e1);
                 if (t < 0.f) { st = ZL_ERR_CUDA; break; }
                 if (tbest < 0.f || t < tbest) { tbest = t; best = v; }

@@ -85,6 +85,9 @@ struct zl_plan_s {
     cudaStream_t h_in = nullptr, h_out = nullptr;
     cudaEvent_t h_start = nullptr, h_in_done[2] = {}, h_comp_done[2] = {}, h_out_done[2] = {};
     int* d_status = nullptr;
+    // device word of the TMA-fed FP32 column kernel: 0, or the code of a bounded wait that
+    // gave up
+    int* d_werr = nullptr;
     mutable zl::StageTimer timer;
     // kernel choice (set by the batch autotuner; defaults = the built-in heuristics):
     // force_plain runs a mixed plan's left inverse on the CUDA-core FP32 kernels instead of
@@ -156,6 +159,11 @@ zl_status tc_prepare(zl_plan_s& p, cudaStream_t s);
 void tc_release(zl_plan_s& p);
 cudaError_t forward_tc(const zl_plan_s& p, const float* x, float* out, int R, cudaStream_t s, Rows rows,
                        const float* scale);
+// TMA-fed FP32 column kernel (k_f32.cu): FP32 data, P_x <= 64, R >= 4, n_x a multiple of 4
+bool f32_column_supported(const zl_plan_s& p, int R);
+cudaError_t forward_column_f32(const zl_plan_s& p, const float* x, const float* M, const float* bx, float* t1, int R,
+                               cudaStream_t s, Rows rows);
+
 cudaError_t tc_read_error(const zl_plan_s& p, int* code);
 cudaError_t tc_clear_error(const zl_plan_s& p);
 

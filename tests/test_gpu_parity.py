@@ -97,11 +97,16 @@ ODD = synth.Workload("odd", 17, 9, 5, 7, 2.0, 0.5, 1.5, 6, "fp32", 41)
 WIDE = synth.Workload("wide", 8, 6, 3, 7, 2.0, 0.6, 1.2, 5, "fp64", 11, tau=0.0)
 TALL = synth.Workload("tall", 8, 6, 6, 3, 2.0, 0.6, 1.2, 5, "fp64", 12, tau=0.0)
 LONG_RING = synth.Workload("long_ring", 300, 1, 3, 12, 9.0, 0.5, 12.0, 9, "fp32", 51)
+# P_x = 60 kept x-frequencies (the widest tile of the register-tiled FP32 column kernel)
+# and P_x = 72 (past it: the per-column kernel)
+PX60 = synth.Workload("px60", 60, 8, 4, 20, 1.5, 0.6, 1.5, 10, "fp32", 61)
+PX72 = synth.Workload("px72", 72, 6, 3, 9, 1.5, 0.6, 1.5, 3, "fp32", 62)
 
 SMALL = [
     (W["c0a_ring"], "fp64"), (W["c0a_plane"], "fp64"), (W["c0b_paper_shape"], "fp64"), (W["c1_ring64"], "fp64"),
     (WIDE, "fp64"), (TALL, "fp64"), (WIDE, "fp32"), (TALL, "fp32"), (ODD, "fp64"), (ODD, "fp32"),
     (RAGGED_C2, "fp32"), (RAGGED_C2, "fp64"), (RAGGED_C3, "fp32"), (RAGGED_C3, "mixed"), (LONG_RING, "fp32"),
+    (PX60, "fp32"), (PX72, "fp32"),
 ]
 
 
