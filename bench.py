@@ -108,6 +108,18 @@ def algorithmic_bytes_per_rhs(w, L, prec, R):
     return sx * (w.n + w.K * L) + sz * w.n * w.K / R
 
 
+# FP32 FMA peak from the unit counts: 148 SMs x 128 FP32 lanes x 2 flops per FMA x the
+# 2032 MHz maximum SM clock (nominal; the CUDA-core kernels are bound by FMA issue)
+FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
+
+
+def column_flops_per_rhs(w, plan):
+    """FMA-pipe flops of the FP32 column kernel per rhs: V1 (K x n_w per column) + x-pass (K x P_x per grid point)."""
+    import numpy as np
+    Px = len(np.unique(plan.modes() % w.Nx))
+    return 2.0 * w.K * (w.nw * w.n + w.Ny * w.Nx * Px)
+
+
 def measured_peak_hbm():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -321,13 +333,25 @@ def run_ours(args, w, prec):
     bpr = algorithmic_bytes_per_rhs(w, plan.L, prec, R)
     peak, peak_kind = measured_peak_hbm()
     achieved = bpr * R / avg_col_s / 1e9
-    kernel_name = "fwd_column_tc_kernel" if (prec == "mixed" and plan_uses_tc(plan)) else "fwd_column_xpass"
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": recorded_traffic(kernel_name, w.name, prec), "kernel": kernel_name,
-                "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback",
-                "kernel_ms_per_launch": avg_col_s * 1e3,
-                "step_frac": bpr * R / (ms / args.steps / 1e3) / 1e9 / peak,
-                "stages_ms_per_launch": {k: (v[1] / v[0] if v[0] else None) for k, v in stages.items()}}
+    if prec == "mixed" and plan_uses_tc(plan):
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                    "traffic": recorded_traffic("fwd_column_tc_kernel", w.name, prec), "kernel": "fwd_column_tc_kernel",
+                    "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback"}
+    elif prec in ("fp32", "mixed"):
+        # the CUDA-core FP32 column kernel is bound by FMA issue: flops against the FP32 peak
+        tflops = column_flops_per_rhs(w, plan) * R / avg_col_s / 1e12
+        roofline = {"bound": "alu", "achieved": tflops, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": tflops / FP32_PEAK_TFLOPS, "traffic": recorded_traffic("fwd_column_f32_kernel", w.name, prec),
+                    "kernel": "fwd_column_f32_kernel (or fwd_column_xpass where its tile does not apply)",
+                    "peak_source": "148 SMs x 128 FP32 FMA lanes x 2 x 2032 MHz (nominal)",
+                    "hbm_frac": achieved / peak}
+    else:
+        roofline = {"bound": "alu", "achieved": None, "peak": None, "unit": "TFLOP/s", "frac": None, "traffic": None,
+                    "kernel": "fwd_column_xpass", "peak_source": "FP64 path: FP64 FMA bound, not measured against a peak",
+                    "hbm_frac": achieved / peak}
+    roofline.update({"kernel_ms_per_launch": avg_col_s * 1e3,
+                     "step_frac": bpr * R / (ms / args.steps / 1e3) / 1e9 / peak,
+                     "stages_ms_per_launch": {k: (v[1] / v[0] if v[0] else None) for k, v in stages.items()}})
 
     # end to end through the host-buffer entry point: H2D of x and D2H of x~ inside every step
     xh = x.cpu().pin_memory()

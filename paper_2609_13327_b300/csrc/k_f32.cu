@@ -84,6 +84,13 @@ __device__ __forceinline__ void fail(volatile int* abort_flag, int* err, int cod
 
 __device__ __forceinline__ void compute_bar() { asm volatile("bar.sync 1, %0;" ::"n"(kCompute) : "memory"); }
 
+// 16-byte global -> shared asynchronous copy of `bytes` (0..16) valid bytes, the rest zero
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, int bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 template <int RC, int NJ>
 __global__ void __launch_bounds__(kThreadsF, 1)
 fwd_column_f32_kernel(const __grid_constant__ CUtensorMap tmap_x, const __grid_constant__ CUtensorMap tmap_p,
@@ -167,9 +174,15 @@ fwd_column_f32_kernel(const __grid_constant__ CUtensorMap tmap_x, const __grid_c
         for (int c = 0; c < nchunk; ++c) {
             const int x0 = c * XC, xn = min(XC, nx - x0), xn4 = (xn + 3) & ~3;
             compute_bar();                               // W, the basis tile and the output tile are free
-            for (int j = warp; j < N; j += kComputeWarps)
-                for (int xc = lane; xc < xn4; xc += 32)
-                    B[j * LD + xc] = (j < Px && xc < xn) ? bx[(size_t)j * nx + x0 + xc] : 0.f;
+            // the basis tile by 16-byte asynchronous copies (zero-filled past P_x and past the
+            // row's end), landing while phase A runs
+            for (int e = tid; e < N * (XC / 4); e += kCompute) {
+                const int j = e / (XC / 4), xc = 4 * (e % (XC / 4));
+                const int valid = (j < Px && xc < xn) ? 4 * min(4, xn - xc) : 0;
+                const float* src = bx + (valid ? (size_t)j * nx + x0 + xc : 0);
+                cp_async16(B + j * LD + xc, src, valid);
+            }
+            cp_async_commit();
             float a[KH][RC];
 #pragma unroll
             for (int k = 0; k < KH; ++k)
@@ -210,6 +223,7 @@ fwd_column_f32_kernel(const __grid_constant__ CUtensorMap tmap_x, const __grid_c
             for (int r = 0; r < RC; ++r)
 #pragma unroll
                 for (int k = 0; k < KH; ++k) W[(r * KC + ah * KH + k) * LD + ax] = live ? a[k][r] : 0.f;
+            cp_async_wait_all();
             compute_bar();
             float part[4][NJ];
 #pragma unroll
@@ -218,21 +232,30 @@ fwd_column_f32_kernel(const __grid_constant__ CUtensorMap tmap_x, const __grid_c
                 for (int j = 0; j < NJ; ++j) part[i][j] = 0.f;
             const float* wp = W + brow * LD;
             const float* bp = B + bcol * LD;
+#pragma unroll 2
             for (int xc = 0; xc < xn4; xc += 4) {
                 float4 wv[4], bv[NJ];
 #pragma unroll
                 for (int i = 0; i < 4; ++i) wv[i] = *reinterpret_cast<const float4*>(wp + 8 * i * LD + xc);
 #pragma unroll
                 for (int j = 0; j < NJ; ++j) bv[j] = *reinterpret_cast<const float4*>(bp + 4 * j * LD + xc);
+                // one component at a time over all 4 x NJ sums: consecutive FMAs are independent
 #pragma unroll
                 for (int i = 0; i < 4; ++i)
 #pragma unroll
-                    for (int j = 0; j < NJ; ++j) {
-                        part[i][j] = fmaf(wv[i].x, bv[j].x, part[i][j]);
-                        part[i][j] = fmaf(wv[i].y, bv[j].y, part[i][j]);
-                        part[i][j] = fmaf(wv[i].z, bv[j].z, part[i][j]);
-                        part[i][j] = fmaf(wv[i].w, bv[j].w, part[i][j]);
-                    }
+                    for (int j = 0; j < NJ; ++j) part[i][j] = fmaf(wv[i].x, bv[j].x, part[i][j]);
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < NJ; ++j) part[i][j] = fmaf(wv[i].y, bv[j].y, part[i][j]);
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < NJ; ++j) part[i][j] = fmaf(wv[i].z, bv[j].z, part[i][j]);
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < NJ; ++j) part[i][j] = fmaf(wv[i].w, bv[j].w, part[i][j]);
             }
 #pragma unroll
             for (int i = 0; i < 4; ++i)

@@ -391,7 +391,7 @@ cudaError_t launch_inv_rc(const zl_plan_s& p, const T* u, const T* M, const T* b
 //     tiles of 8 rows x 4 columns over 128-bit shared loads of the transposed u tile and
 //     of the basis (lanes: 4 row groups x 8 column groups, warps: 4 x 2);
 //   phase 2 (per-column product): out[r][l][x] += sum_k M[k][l][x] Y[(r, k)][x], thread =
-//     (column, quarter of the levels) with its RC x NLQ sums in registers across the
+//     (column, levels q + 4 i for its q < 4) with its RC x NLQ sums in registers across the
 //     member chunks; each member-matrix element is read once per CTA.
 // CTAs of the same row and column chunk (different rhs) are adjacent, so the
 // member-matrix tile they share is read from L2.
@@ -425,7 +425,7 @@ inv_column_sgemm(const float* __restrict__ u, const float* __restrict__ M, const
     const int rg = (warp & 3) * 4 + (lane & 3);        // rows 4 rg + i and 64 + 4 rg + i (i < 4)
     const int cg = (warp >> 2) * 8 + (lane >> 2);      // columns 4 cg + j (j < 4)
     const int xc2 = tid & (kIvXC - 1);                 // phase 2: column
-    const int l0 = (tid / kIvXC) * NLQ;                // phase 2: first level
+    const int lq = tid / kIvXC;                        // phase 2: levels lq + 4 i (i < NLQ)
     const bool col_ok = xc2 < xn;
     const long long m = (long long)y * nx + x0 + xc2;
 
@@ -480,7 +480,7 @@ inv_column_sgemm(const float* __restrict__ u, const float* __restrict__ M, const
 #pragma unroll
                     for (int i = 0; i < NLQ; ++i)
                         mv[h][i] = __ldg(Mm + ((unsigned)min(k0 + kk + h, K - 1) * (unsigned)nw +
-                                               (unsigned)min(l0 + i, nw - 1)) * nhu);
+                                               (unsigned)min(lq + 4 * i, nw - 1)) * nhu);
 #pragma unroll
                 for (int h = 0; h < KU; ++h) {
                     float yv[RC];
@@ -499,7 +499,7 @@ inv_column_sgemm(const float* __restrict__ u, const float* __restrict__ M, const
     for (int r = 0; r < RC; ++r)
 #pragma unroll
         for (int i = 0; i < NLQ; ++i)
-            if (r0 + r < R && l0 + i < nw) out[((long long)(r0 + r) * nw + l0 + i) * nh + m] = acc[r][i];
+            if (r0 + r < R && lq + 4 * i < nw) out[((long long)(r0 + r) * nw + lq + 4 * i) * nh + m] = acc[r][i];
 }
 
 template <int RC>
