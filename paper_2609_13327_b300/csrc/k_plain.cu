@@ -1074,6 +1074,12 @@ cudaError_t inverse_plain(const zl_plan_s& p, const Tables<T>& t, const T* M, co
     p.timer.end(s);
     if (e != cudaSuccess) return e;
     if constexpr (sizeof(T) == 4) {
+        if (f32_inverse_supported(p, R)) {
+            p.timer.begin(ZL_STAGE_INV_COLUMN, s);
+            e = inverse_column_f32(p, u, M, t.bx, out, R, s);
+            p.timer.end(s);
+            if (e != cudaErrorNotSupported) return e;
+        }
         if (inv_sgemm_rc(p, R) > 0) {
             p.timer.begin(ZL_STAGE_INV_COLUMN, s);
             e = launch_inv_sgemm_any(p, u, M, t.bx, out, R, s);

@@ -163,6 +163,10 @@ cudaError_t forward_tc(const zl_plan_s& p, const float* x, float* out, int R, cu
 bool f32_column_supported(const zl_plan_s& p, int R);
 cudaError_t forward_column_f32(const zl_plan_s& p, const float* x, const float* M, const float* bx, float* t1, int R,
                                cudaStream_t s, Rows rows);
+// TMA-fed FP32 inverse column pass (k_f32.cu): FP32 data, P_x <= 64, n_w <= 64, R >= 2, n_x a multiple of 4
+bool f32_inverse_supported(const zl_plan_s& p, int R);
+cudaError_t inverse_column_f32(const zl_plan_s& p, const float* u, const float* M, const float* bx, float* out, int R,
+                               cudaStream_t s);
 
 cudaError_t tc_read_error(const zl_plan_s& p, int* code);
 cudaError_t tc_clear_error(const zl_plan_s& p);
