@@ -117,7 +117,7 @@ def column_flops_per_rhs(w, plan):
     """FMA-pipe flops of the FP32 column kernel per rhs: V1 (K x n_w per column) + x-pass (K x P_x per grid point)."""
     import numpy as np
     Px = len(np.unique(plan.modes() % w.Nx))
-    return 2.0 * w.K * (w.nw * w.n + w.Ny * w.Nx * Px)
+    return 2.0 * w.K * (w.nw * w.Nx * w.Ny + w.Ny * w.Nx * Px)
 
 
 def measured_peak_hbm():

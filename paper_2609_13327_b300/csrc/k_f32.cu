@@ -6,7 +6,8 @@
 // (r, k) of the x-pass GEMM
 //     t1[y][r][k][jx] = sum_x W[r][k][x] bx[jx][x],   W[r][k][x] = sum_l P[k][l][x] x[r][l][x],
 // processed in chunks of 128 grid columns.  One copy-issuing thread streams the chunk's
-// x tile [RC][LV][128] and member-matrix tile [KC][LV][128], LV levels per stage, into a
+// x tile [RC][LV][128] and member-matrix tile [KC][LV][128], LV levels per stage (4 with 8
+// rhs per unit, else 2), into a
 // ring of shared-memory stages with 3-D tensor copies (out-of-range levels, rhs and
 // members arrive as zeros), running ahead across chunks and units.  Eight compute warps:
 //   phase A (V1): thread = (column, half of the members), its KC/2 x RC sums in
@@ -43,7 +44,8 @@ constexpr int kCompute = 32 * kComputeWarps;
 constexpr int kThreadsF = kCompute + 32;      // + the copy-issuing warp
 constexpr int XC = 128;                       // grid columns per chunk
 constexpr int LD = XC + 4;                    // row stride (words) of W and of the basis tile
-constexpr int LV = 2;                         // levels per stage
+// levels per stage of the forward kernel: 4 with 8 rhs per unit (a 48 KB stage), else 2
+__host__ __device__ constexpr int lv_of(int RC) { return RC >= 8 ? 4 : 2; }
 constexpr int kMaxStages = 6;
 constexpr unsigned long long kWaitCycles = 4000000000ull;   // ~2 s at 2 GHz
 
@@ -59,7 +61,7 @@ __host__ __device__ inline FPlan fplan(int RC, int N, int nstage) {
     f.w = 0;                                                    // W [128][LD], then the output tile
     f.b = f.w + 128u * LD * 4u;                                 // basis tile [N][LD]
     f.ring = (f.b + (uint32_t)N * LD * 4u + 127u) & ~127u;      // stages: x [RC][LV][XC], P [KC][LV][XC]
-    f.stage = (uint32_t)(RC + KC) * LV * XC * 4u;
+    f.stage = (uint32_t)(RC + KC) * lv_of(RC) * XC * 4u;
     f.bars = f.ring + (uint32_t)nstage * f.stage;
     f.total = f.bars + B_COUNT * 8u + 8u;                       // + the abort flag
     return f;
@@ -110,6 +112,7 @@ fwd_column_f32_kernel(const __grid_constant__ CUtensorMap tmap_x, const __grid_c
     const int nkc = (K + KC - 1) / KC, nrc = (R + RC - 1) / RC;
     const int units = ny * nrc * nkc;
     const int nchunk = (nx + XC - 1) / XC;
+    constexpr int LV = lv_of(RC);
     const int nlg = (nw + LV - 1) / LV;
 
     if (tid == 0) {
@@ -232,7 +235,7 @@ fwd_column_f32_kernel(const __grid_constant__ CUtensorMap tmap_x, const __grid_c
                 for (int j = 0; j < NJ; ++j) part[i][j] = 0.f;
             const float* wp = W + brow * LD;
             const float* bp = B + bcol * LD;
-#pragma unroll 2
+#pragma unroll 4
             for (int xc = 0; xc < xn4; xc += 4) {
                 float4 wv[4], bv[NJ];
 #pragma unroll
@@ -298,11 +301,12 @@ EncodeTiledFn encode_fn() {
     return fn;
 }
 
-// 3-D map of a [n2][n1][n0] FP32 array with box {XC, LV, b2}.
-bool encode3(CUtensorMap* m, const float* base, cuuint64_t n0, cuuint64_t n1, cuuint64_t n2, cuuint32_t b2) {
+// 3-D map of a [n2][n1][n0] FP32 array with box {XC, b1, b2}.
+bool encode3(CUtensorMap* m, const float* base, cuuint64_t n0, cuuint64_t n1, cuuint64_t n2, cuuint32_t b1,
+             cuuint32_t b2) {
     const cuuint64_t gdim[3] = {n0, n1, n2};
     const cuuint64_t gstride[2] = {n0 * sizeof(float), n0 * n1 * sizeof(float)};
-    const cuuint32_t box[3] = {(cuuint32_t)XC, (cuuint32_t)LV, b2};
+    const cuuint32_t box[3] = {(cuuint32_t)XC, b1, b2};
     const cuuint32_t estride[3] = {1, 1, 1};
     return encode_fn()(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base), gdim, gstride, box, estride,
                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -316,8 +320,8 @@ cudaError_t launch_f32(const zl_plan_s& p, const float* x, const float* M, const
                        cudaStream_t s, Rows rows) {
     constexpr int KC = 128 / RC;
     CUtensorMap tx, tp;
-    if (!encode3(&tx, x, (cuuint64_t)rows.ny * p.d.nx, p.d.nw, R, RC) ||
-        !encode3(&tp, M, (cuuint64_t)p.nh, p.d.nw, p.d.K, KC))
+    if (!encode3(&tx, x, (cuuint64_t)rows.ny * p.d.nx, p.d.nw, R, lv_of(RC), RC) ||
+        !encode3(&tp, M, (cuuint64_t)p.nh, p.d.nw, p.d.K, lv_of(RC), KC))
         return cudaErrorNotSupported;
     const FPlan f0 = fplan(RC, 8 * NJ, 0);
     const int nstage = std::min<int>(kMaxStages, (int)((227u * 1024u - f0.total) / f0.stage));

@@ -685,37 +685,50 @@ fwd_ypass_gemm(const T* __restrict__ t1, const T* __restrict__ byk, const int* _
 
 // FP32 y-pass as one register-tiled GEMM over all pairs:
 //   D[i][n] = sum_y byk[y][i] t1[y][n],   n = pair * Px + jx (the flattened t1 row),
-// then x~[pair][j] = scale_j D[ipy_j][pair * Px + jx_j].  A CTA owns 64 consecutive
+// then x~[pair][j] = scale_j D[ipy_j][pair * Px + jx_j].  A CTA owns 64 CPT consecutive
 // columns n (a pair may straddle two CTAs; each writes the modes whose column it holds)
-// and all kept y-frequencies: thread = (column, group of PYG y-frequencies), the column's
-// t1 value and a broadcast 128-bit basis load per 4 products.  The t1 and basis rows of
-// the next 32 values of y are loaded into registers while the current ones are used.
-constexpr int kYsN = 64;                 // columns per CTA
-constexpr int kYsY = 32;                 // rows of y per chunk
+// and all kept y-frequencies: thread = (CPT columns n + 64 c, group of PYG
+// y-frequencies), CPT t1 values and one broadcast 128-bit basis load per 4 CPT products.
+// The t1 and basis rows of the next 32 (16 with 4 columns per thread) values of y are
+// loaded into registers while the current ones are used; the output tile reuses the
+// shared memory of the stream.
+constexpr int kYsN = 64;                 // columns per CTA and column slot
 
-template <int PYG>
+template <int PYG, int CPT>
+struct YsPlan {
+    static constexpr int YC = CPT >= 4 ? 16 : 32;  // rows of y per chunk
+    static constexpr int IG = kThreads / kYsN;
+    static constexpr int PYT = IG * PYG;           // kept y-frequencies covered (>= Py)
+    static constexpr int NC = kYsN * CPT;          // columns per CTA
+    static constexpr size_t stream = ((size_t)YC * NC + (size_t)YC * PYT) * sizeof(float);
+    static constexpr size_t tile = (size_t)PYT * (NC + 1) * sizeof(float);
+    static constexpr size_t bytes = stream > tile ? stream : tile;
+};
+
+template <int PYG, int CPT>
 __global__ void __launch_bounds__(kThreads)
 fwd_ypass_sgemm(const float* __restrict__ t1, const float* __restrict__ byk, const int* __restrict__ m_ipy,
                 const int* __restrict__ m_jx, const float* __restrict__ scale, float* __restrict__ out, int npairs,
                 int ny, int Px, int L, int pys) {
-    constexpr int IG = kThreads / kYsN;
-    constexpr int PYT = IG * PYG;                  // kept y-frequencies covered (>= Py)
-    constexpr int TQ = kYsY * kYsN / kThreads;     // t1 values per thread per chunk
+    using YP = YsPlan<PYG, CPT>;
+    constexpr int PYT = YP::PYT, NC = YP::NC, kYsY = YP::YC;
+    constexpr int TQ = kYsY * NC / kThreads;       // t1 values per thread per chunk
     constexpr int BQ = (kYsY * PYT + kThreads - 1) / kThreads;
     static_assert(PYG % 4 == 0, "128-bit basis loads");
-    __shared__ float Ts[kYsY][kYsN];
-    __shared__ __align__(16) float Bs[kYsY][PYT];
-    __shared__ float Ds[PYT][kYsN + 1];
+    extern __shared__ float4 ys_smem4[];
+    float* Ts = reinterpret_cast<float*>(ys_smem4);  // [kYsY][NC]
+    float* Bs = Ts + kYsY * NC;                      // [kYsY][PYT]
+    float* Ds = Ts;                                  // [PYT][NC + 1], after the stream
     const int tid = threadIdx.x;
     const int n = tid % kYsN, g = tid / kYsN;
     const long long ncols = (long long)npairs * Px;
-    const long long n0 = (long long)blockIdx.x * kYsN;
+    const long long n0 = (long long)blockIdx.x * NC;
 
     float tr[TQ], br[BQ];
     auto fetch = [&](int y0) {
 #pragma unroll
         for (int q = 0; q < TQ; ++q) {
-            const int e = tid + q * kThreads, row = e / kYsN, col = e % kYsN;
+            const int e = tid + q * kThreads, row = e / NC, col = e % NC;
             tr[q] = (y0 + row < ny && n0 + col < ncols) ? t1[(long long)(y0 + row) * ncols + n0 + col] : 0.f;
         }
 #pragma unroll
@@ -724,64 +737,85 @@ fwd_ypass_sgemm(const float* __restrict__ t1, const float* __restrict__ byk, con
             br[q] = (e < kYsY * PYT && y0 + row < ny && i < pys) ? byk[(long long)(y0 + row) * pys + i] : 0.f;
         }
     };
-    float acc[PYG];
+    float acc[CPT][PYG];
 #pragma unroll
-    for (int i = 0; i < PYG; ++i) acc[i] = 0.f;
+    for (int c = 0; c < CPT; ++c)
+#pragma unroll
+        for (int i = 0; i < PYG; ++i) acc[c][i] = 0.f;
     fetch(0);
     for (int y0 = 0; y0 < ny; y0 += kYsY) {
         __syncthreads();                               // the previous chunk has been used
 #pragma unroll
-        for (int q = 0; q < TQ; ++q) {
-            const int e = tid + q * kThreads;
-            Ts[e / kYsN][e % kYsN] = tr[q];
-        }
+        for (int q = 0; q < TQ; ++q) Ts[tid + q * kThreads] = tr[q];
 #pragma unroll
         for (int q = 0; q < BQ; ++q) {
             const int e = tid + q * kThreads;
-            if (e < kYsY * PYT) Bs[e / PYT][e % PYT] = br[q];
+            if (e < kYsY * PYT) Bs[e] = br[q];
         }
         __syncthreads();
         if (y0 + kYsY < ny) fetch(y0 + kYsY);
-#pragma unroll 4
+#pragma unroll 2
         for (int yy = 0; yy < kYsY; ++yy) {
-            const float t = Ts[yy][n];
-            const float4* b = reinterpret_cast<const float4*>(&Bs[yy][g * PYG]);
+            float t[CPT];
+#pragma unroll
+            for (int c = 0; c < CPT; ++c) t[c] = Ts[yy * NC + n + kYsN * c];
+            const float4* b = reinterpret_cast<const float4*>(Bs + yy * PYT + g * PYG);
 #pragma unroll
             for (int q = 0; q < PYG / 4; ++q) {
                 const float4 bv = b[q];
-                acc[4 * q] = fmaf(bv.x, t, acc[4 * q]);
-                acc[4 * q + 1] = fmaf(bv.y, t, acc[4 * q + 1]);
-                acc[4 * q + 2] = fmaf(bv.z, t, acc[4 * q + 2]);
-                acc[4 * q + 3] = fmaf(bv.w, t, acc[4 * q + 3]);
+#pragma unroll
+                for (int c = 0; c < CPT; ++c) {
+                    acc[c][4 * q] = fmaf(bv.x, t[c], acc[c][4 * q]);
+                    acc[c][4 * q + 1] = fmaf(bv.y, t[c], acc[c][4 * q + 1]);
+                    acc[c][4 * q + 2] = fmaf(bv.z, t[c], acc[c][4 * q + 2]);
+                    acc[c][4 * q + 3] = fmaf(bv.w, t[c], acc[c][4 * q + 3]);
+                }
             }
         }
     }
+    __syncthreads();                                   // the stream buffers become the output tile
 #pragma unroll
-    for (int i = 0; i < PYG; ++i) Ds[g * PYG + i][n] = acc[i];
+    for (int c = 0; c < CPT; ++c)
+#pragma unroll
+        for (int i = 0; i < PYG; ++i) Ds[(g * PYG + i) * (NC + 1) + n + kYsN * c] = acc[c][i];
     __syncthreads();
     const long long p_lo = n0 / Px;
-    const long long p_hi = min((long long)npairs - 1, (n0 + kYsN - 1) / Px);
+    const long long p_hi = min((long long)npairs - 1, (n0 + NC - 1) / Px);
     for (long long pr = p_lo; pr <= p_hi; ++pr) {
         const long long c0 = pr * Px - n0;             // column of the pair's x-frequency 0
         for (int j = tid; j < L; j += kThreads) {
             const long long col = c0 + m_jx[j];
-            if (col < 0 || col >= kYsN) continue;
-            const float v = Ds[m_ipy[j]][col];
+            if (col < 0 || col >= NC) continue;
+            const float v = Ds[m_ipy[j] * (NC + 1) + col];
             out[pr * L + j] = scale ? v * scale[j] : v;
         }
     }
 }
 
+template <int PYG, int CPT>
+cudaError_t launch_ypass_sgemm_cpt(const zl_plan_s& p, const float* t1, const float* byk, const int* m_ipy,
+                                   const int* m_jx, const float* scale, float* out, int R, cudaStream_t s, Rows rows) {
+    using YP = YsPlan<PYG, CPT>;
+    const long long npairs = (long long)R * p.d.K;
+    const long long grid = (npairs * p.Px + YP::NC - 1) / YP::NC;
+    cudaError_t e = cudaFuncSetAttribute(fwd_ypass_sgemm<PYG, CPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)YP::bytes);
+    if (e != cudaSuccess) return e;
+    p.timer.begin(ZL_STAGE_FWD_YPASS, s);
+    fwd_ypass_sgemm<PYG, CPT><<<(unsigned)grid, kThreads, YP::bytes, s>>>(
+        t1, byk + (size_t)rows.y0 * p.pys, m_ipy, m_jx, scale, out, (int)npairs, rows.ny, p.Px, p.L, p.pys);
+    p.timer.end(s);
+    return cudaGetLastError();
+}
+
+// columns per thread: 4 while that still leaves about two CTAs per SM, else 1
 template <int PYG>
 cudaError_t launch_ypass_sgemm(const zl_plan_s& p, const float* t1, const float* byk, const int* m_ipy,
                                const int* m_jx, const float* scale, float* out, int R, cudaStream_t s, Rows rows) {
-    const long long npairs = (long long)R * p.d.K;
-    const long long grid = (npairs * p.Px + kYsN - 1) / kYsN;
-    p.timer.begin(ZL_STAGE_FWD_YPASS, s);
-    fwd_ypass_sgemm<PYG><<<(unsigned)grid, kThreads, 0, s>>>(t1, byk + (size_t)rows.y0 * p.pys, m_ipy, m_jx, scale,
-                                                             out, (int)npairs, rows.ny, p.Px, p.L, p.pys);
-    p.timer.end(s);
-    return cudaGetLastError();
+    const long long ncols = (long long)R * p.d.K * p.Px;
+    if (ncols >= 2LL * 148 * 4 * kYsN)
+        return launch_ypass_sgemm_cpt<PYG, 4>(p, t1, byk, m_ipy, m_jx, scale, out, R, s, rows);
+    return launch_ypass_sgemm_cpt<PYG, 1>(p, t1, byk, m_ipy, m_jx, scale, out, R, s, rows);
 }
 
 // FP32 y-pass with the t1 rows of the CTA's pairs and the kept y-basis rows streamed
