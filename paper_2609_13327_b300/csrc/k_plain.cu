@@ -204,22 +204,24 @@ inv_ypass(const T* __restrict__ c, const T* __restrict__ by, const int* __restri
 //   mode j = (i-th kept y-frequency, jx-th kept x-frequency), 0 for the others.
 // C is built in shared memory with its columns grouped as [i][jx % 4][jx / 4] so that a
 // thread's QJ x-frequencies (jx = g + 4 q, g = its group) are QJ consecutive words; the
-// kept y-basis is staged 64 rows at a time; thread (row yy, group g) accumulates its QJ
-// outputs with one basis load and QJ / 4 vector loads of C per kept y-frequency, and the
-// 64 x Px output tile leaves through shared memory with coalesced stores.
+// kept y-basis is staged 64 MY rows at a time; thread (rows yy + 64 m for m < MY, group g)
+// accumulates its MY x QJ outputs with MY basis loads and QJ / 4 vector loads of C per
+// kept y-frequency, and the output tile leaves through shared memory with coalesced
+// stores.
 // ---------------------------------------------------------------------------
 constexpr int kInvYRows = 64;
 
-template <typename T, int QJ>
+template <typename T, int QJ, int MY>
 __global__ void __launch_bounds__(kThreads)
 inv_ypass_dense(const T* __restrict__ c, const T* __restrict__ byk, const int* __restrict__ m_ipy,
                 const int* __restrict__ m_jx, const T* __restrict__ scale, T* __restrict__ u, int K, int ny, int Px,
                 int L, int Py, int pys) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int CW = 4 * QJ;                           // C row width (x-frequency slots)
+    constexpr int YT = kInvYRows * MY;                   // rows of y per tile
     T* C = reinterpret_cast<T*>(smem_raw);               // [Py][4][QJ]
-    T* bys = C + (size_t)Py * CW;                        // [kInvYRows][Py + 1]
-    T* ot = bys + (size_t)kInvYRows * (Py + 1);          // [kInvYRows][Px]
+    T* bys = C + (size_t)Py * CW;                        // [YT][Py + 1]
+    T* ot = bys + (size_t)YT * (Py + 1);                 // [YT][Px]
     const int k = blockIdx.x, r = blockIdx.y;
     const T* src = c + ((long long)r * K + k) * L;
     for (int e = threadIdx.x; e < Py * CW; e += blockDim.x) C[e] = T(0);
@@ -230,29 +232,40 @@ inv_ypass_dense(const T* __restrict__ c, const T* __restrict__ byk, const int* _
     }
     const int yy = threadIdx.x % kInvYRows, g = threadIdx.x / kInvYRows;   // g = 0..3
     T* dst = u + ((long long)r * K + k) * ny * Px;
-    for (int y0 = 0; y0 < ny; y0 += kInvYRows) {
-        const int yn = min(kInvYRows, ny - y0);
+    for (int y0 = 0; y0 < ny; y0 += YT) {
+        const int yn = min(YT, ny - y0);
         __syncthreads();                                  // C complete; previous tile written out
         for (int e = threadIdx.x; e < yn * Py; e += blockDim.x) {
             const int a = e / Py, i = e - a * Py;
             bys[(size_t)a * (Py + 1) + i] = byk[(size_t)(y0 + a) * pys + i];
         }
         __syncthreads();
-        T acc[QJ];
+        T acc[MY][QJ];
 #pragma unroll
-        for (int q = 0; q < QJ; ++q) acc[q] = T(0);
-        if (yy < yn) {
-            const T* brow = bys + (size_t)yy * (Py + 1);
-            for (int i = 0; i < Py; ++i) {
-                const T b = brow[i];
-                const T* crow = C + (size_t)i * CW + g * QJ;
+        for (int m = 0; m < MY; ++m)
 #pragma unroll
-                for (int q = 0; q < QJ; ++q) acc[q] = fma(b, crow[q], acc[q]);
-            }
+            for (int q = 0; q < QJ; ++q) acc[m][q] = T(0);
+        const T* crow = C + g * QJ;
+        for (int i = 0; i < Py; ++i, crow += CW) {
+            T b[MY];
+#pragma unroll
+            for (int m = 0; m < MY; ++m) b[m] = bys[(size_t)(yy + kInvYRows * m) * (Py + 1) + i];
 #pragma unroll
             for (int q = 0; q < QJ; ++q) {
-                const int jx = g + 4 * q;
-                if (jx < Px) ot[(size_t)yy * Px + jx] = acc[q];
+                const T cv = crow[q];
+#pragma unroll
+                for (int m = 0; m < MY; ++m) acc[m][q] = fma(b[m], cv, acc[m][q]);
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < MY; ++m) {
+            const int row = yy + kInvYRows * m;
+            if (row < yn) {
+#pragma unroll
+                for (int q = 0; q < QJ; ++q) {
+                    const int jx = g + 4 * q;
+                    if (jx < Px) ot[(size_t)row * Px + jx] = acc[m][q];
+                }
             }
         }
         __syncthreads();
@@ -260,15 +273,32 @@ inv_ypass_dense(const T* __restrict__ c, const T* __restrict__ byk, const int* _
     }
 }
 
+template <typename T, int QJ, int MY>
+size_t inv_ypass_dense_smem(const zl_plan_s& p) {
+    return ((size_t)p.Py * 4 * QJ + (size_t)kInvYRows * MY * (p.Py + 1) + (size_t)kInvYRows * MY * p.Px) * sizeof(T);
+}
+
+template <typename T, int QJ, int MY>
+cudaError_t launch_inv_ypass_dense_my(const zl_plan_s& p, const Tables<T>& t, const T* scale, const T* c, T* u, int R,
+                                      cudaStream_t s) {
+    const size_t smem = inv_ypass_dense_smem<T, QJ, MY>(p);
+    cudaError_t e = cudaFuncSetAttribute(inv_ypass_dense<T, QJ, MY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    inv_ypass_dense<T, QJ, MY><<<dim3(p.d.K, R), kThreads, smem, s>>>(c, t.byk, t.m_ipy, t.m_jx, scale, u, p.d.K,
+                                                                       p.d.ny, p.Px, p.L, p.Py, p.pys);
+    return cudaGetLastError();
+}
+
+// rows per thread: 2 when the grid has 128 rows or more and the tile fits two CTAs per SM,
+// else 1 (4 rows per thread, with fewer CTAs per SM, was slower at the larger grids)
 template <typename T, int QJ>
 cudaError_t launch_inv_ypass_dense(const zl_plan_s& p, const Tables<T>& t, const T* scale, const T* c, T* u, int R,
                                    cudaStream_t s) {
-    const size_t smem = ((size_t)p.Py * 4 * QJ + (size_t)kInvYRows * (p.Py + 1) + (size_t)kInvYRows * p.Px) * sizeof(T);
-    cudaError_t e = cudaFuncSetAttribute(inv_ypass_dense<T, QJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    inv_ypass_dense<T, QJ><<<dim3(p.d.K, R), kThreads, smem, s>>>(c, t.byk, t.m_ipy, t.m_jx, scale, u, p.d.K, p.d.ny,
-                                                                   p.Px, p.L, p.Py, p.pys);
-    return cudaGetLastError();
+    constexpr size_t kTwoPerSm = 110 * 1024;
+    if (p.d.ny >= 2 * kInvYRows && inv_ypass_dense_smem<T, QJ, 2>(p) <= kTwoPerSm)
+        return launch_inv_ypass_dense_my<T, QJ, 2>(p, t, scale, c, u, R, s);
+    return launch_inv_ypass_dense_my<T, QJ, 1>(p, t, scale, c, u, R, s);
 }
 
 // ---------------------------------------------------------------------------

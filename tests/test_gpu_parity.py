@@ -101,12 +101,16 @@ LONG_RING = synth.Workload("long_ring", 300, 1, 3, 12, 9.0, 0.5, 12.0, 9, "fp32"
 # and P_x = 72 (past it: the per-column kernel)
 PX60 = synth.Workload("px60", 60, 8, 4, 20, 1.5, 0.6, 1.5, 10, "fp32", 61)
 PX72 = synth.Workload("px72", 72, 6, 3, 9, 1.5, 0.6, 1.5, 3, "fp32", 62)
+# 40 levels: 10 level groups of the TMA-fed forward kernel, 2 rhs per CTA in the TMA-fed
+# inverse pass; in mixed precision the tensor-core kernel does not take n_w > 32, so the
+# mixed plan runs the FP32 CUDA-core kernels
+LEVELS40 = synth.Workload("levels40", 24, 16, 40, 56, 3.0, 0.7, 3.0, 6, "fp32", 71)
 
 SMALL = [
     (W["c0a_ring"], "fp64"), (W["c0a_plane"], "fp64"), (W["c0b_paper_shape"], "fp64"), (W["c1_ring64"], "fp64"),
     (WIDE, "fp64"), (TALL, "fp64"), (WIDE, "fp32"), (TALL, "fp32"), (ODD, "fp64"), (ODD, "fp32"),
     (RAGGED_C2, "fp32"), (RAGGED_C2, "fp64"), (RAGGED_C3, "fp32"), (RAGGED_C3, "mixed"), (LONG_RING, "fp32"),
-    (PX60, "fp32"), (PX72, "fp32"),
+    (PX60, "fp32"), (PX72, "fp32"), (LEVELS40, "fp32"), (LEVELS40, "mixed"),
 ]
 
 
