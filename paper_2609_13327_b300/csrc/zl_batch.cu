@@ -83,7 +83,7 @@ void read_tune_file() {
         const size_t bar = s.rfind('|');
         if (bar == std::string::npos) continue;
         const int v = std::atoi(s.c_str() + bar + 1);
-        if (v >= 0 && v <= 4) g_tune_cache[s.substr(0, bar)] = v;
+        if (v >= 0 && v < kVariants) g_tune_cache[s.substr(0, bar)] = v;
     }
     std::fclose(f);
 }
