@@ -18,6 +18,11 @@
 // The x-pass is fused with the per-column product: a CTA owns one grid row, so
 // the regrouping of w^(m) into member segments (steps V2-V3, the paper's
 // inter-processor exchange) never leaves shared memory.
+//
+// For FP32 data the TMA-fed persistent column kernels of k_f32.cu take the forward
+// and inverse column passes wherever their tiles apply (dispatch in launch_fwd and
+// inverse_plain); the kernels here serve FP64 and the remaining FP32 shapes, and the
+// FP32 y-passes (fwd_ypass_sgemm, inv_ypass_dense) serve both.
 
 #include "zl_internal.cuh"
 
