@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 fwd_ypass_tc_kernel(const __grid_constant__ CUtensorMap tmap_t, const __half* __restrict__ bimg,
                     const unsigned* __restrict__ t1max, const int* __restrict__ m_ipy, const int* __restrict__ m_jx,
                     const float* __restrict__ scale, float* __restrict__ out, int* __restrict__ err, int npairs,
-                    int ldp, int ppu, int L, int nstage_y, int resident) {
+                    int ldp, int ppu, int L, int nstage_y, int resident, int staged_tab) {
     constexpr int PYB = NB / 2;
     extern __shared__ __align__(1024) uint8_t smem[];
     const int rows_u = ppu * ldp;
@@ -310,6 +310,16 @@ fwd_ypass_tc_kernel(const __grid_constant__ CUtensorMap tmap_t, const __half* __
         const float unscale = ldexpf(1.0f, e2 - 14) / kBasisScale;
         const uint32_t lane_off = (uint32_t)(32 * q) << 16;
         constexpr int GP = PYB + 1;                                // gather row pitch (odd)
+        // the mode table (offset of mode j in a pair's gather rows, and its scale) in shared
+        // memory after the barriers when it fits, read once per CTA instead of per pair; the
+        // first B_GFULL wait below orders these writes before every epilogue thread's reads
+        int* tab_off = reinterpret_cast<int*>(smem + sp.total);
+        float* tab_scale = reinterpret_cast<float*>(tab_off + L);
+        if (staged_tab)
+            for (int j = et; j < L; j += 128) {
+                tab_off[j] = m_jx[j] * GP + m_ipy[j];
+                tab_scale[j] = scale ? scale[j] : 1.0f;
+            }
         bool ok = true;
         for (int ui = 0; ui < my_units && ok; ++ui) {
             const int u = (int)blockIdx.x + ui * (int)gridDim.x;
@@ -332,9 +342,14 @@ fwd_ypass_tc_kernel(const __grid_constant__ CUtensorMap tmap_t, const __half* __
                 const int pair = p0 + pl;
                 if (pair >= npairs) break;
                 float* o = out + (size_t)pair * L;
-                for (int j = et; j < L; j += 128) {
-                    const float g = gather[(pl * ldp + m_jx[j]) * GP + m_ipy[j]];
-                    o[j] = scale ? g * scale[j] : g;
+                if (staged_tab) {
+                    const float* gp = gather + pl * ldp * GP;
+                    for (int j = et; j < L; j += 128) o[j] = gp[tab_off[j]] * tab_scale[j];
+                } else {
+                    for (int j = et; j < L; j += 128) {
+                        const float g = gather[(pl * ldp + m_jx[j]) * GP + m_ipy[j]];
+                        o[j] = scale ? g * scale[j] : g;
+                    }
                 }
             }
             mbar_arrive(&bars[B_GFREE]);
@@ -498,10 +513,15 @@ cudaError_t forward_ypass_tc(const zl_plan_s& p, const float* t1, int ldp, const
     if (cr != CUDA_SUCCESS) return cudaErrorInvalidValue;
     const int units = (npairs + ppu - 1) / ppu;
     const int grid = std::min(units, 148);
+    // the mode table goes to shared memory when it fits next to the kernel's plan
+    const size_t tab_bytes = (size_t)p.L * 8u;
+    const int staged_tab = (size_t)t.smem + tab_bytes <= 227u * 1024u ? 1 : 0;
+    const size_t smem = t.smem + (staged_tab ? tab_bytes : 0);
     p.timer.begin(ZL_STAGE_FWD_YPASS, s);
 #define ZL_YTC_LAUNCH(NBV)                                                                                           \
-    fwd_ypass_tc_kernel<NBV><<<grid, kThreads, t.smem, s>>>(tmap, t.bimg, t.t1max, p.tf.m_ipy, p.tf.m_jx, scale, out, \
-                                                            t.d_err, npairs, ldp, ppu, p.L, t.nstage_y, t.resident)
+    fwd_ypass_tc_kernel<NBV><<<grid, kThreads, smem, s>>>(tmap, t.bimg, t.t1max, p.tf.m_ipy, p.tf.m_jx, scale, out, \
+                                                          t.d_err, npairs, ldp, ppu, p.L, t.nstage_y, t.resident,   \
+                                                          staged_tab)
     switch (nb) {
         case 16: ZL_YTC_LAUNCH(16); break;
         case 32: ZL_YTC_LAUNCH(32); break;
