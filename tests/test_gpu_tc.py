@@ -38,6 +38,18 @@ CASES = [
     synth.Workload("tc_py47", 64, 64, 16, 48, 6.0, 0.7, 3.0, 19, "mixed", 36),
     synth.Workload("tc_py31", 64, 64, 24, 40, 6.0, 0.75, 4.5, 23, "mixed", 37),
     synth.Workload("tc_py17", 64, 48, 8, 32, 4.0, 0.7, 6.0, 11, "mixed", 38),
+    # n_w = K (the paper's square A_m, Eq. nwEqualsK): Zh^- is a true left inverse there
+    synth.Workload("tc_square_16", 32, 16, 16, 16, 3.0, 0.7, 3.0, 16, "mixed", 51),
+    synth.Workload("tc_square_32", 32, 8, 32, 32, 3.0, 0.7, 3.0, 16, "mixed", 52),
+    # n_w > K: the least-squares pseudo-inverse (AᵀA)^{-1} Aᵀ of each column
+    synth.Workload("tc_tall_24_16", 48, 16, 24, 16, 4.0, 0.7, 4.0, 16, "mixed", 54),
+    synth.Workload("tc_tall_32_20", 32, 16, 32, 20, 4.0, 0.7, 4.0, 19, "mixed", 55),
+]
+
+# n_w = K with every mode kept (tau = 0): Zh is square and Zh^- Zh = I (Sec. 3.9)
+SQUARE_ALL_MODES = [
+    synth.Workload("tc_square_16_all_modes", 16, 8, 16, 16, 3.0, 0.7, 1.0, 16, "mixed", 61, tau=0.0),
+    synth.Workload("tc_square_32_all_modes", 32, 8, 32, 32, 3.0, 0.7, 1.0, 16, "mixed", 62, tau=0.0),
 ]
 
 
@@ -53,6 +65,41 @@ def test_tensor_core_left_inverse(zl, w):
     assert plan.device_error() == 0
     ref = swift.apply_left_inverse(oracle, x.astype(np.float64))
     compare.check(out, ref, TOL_MIXED, 2, w.name)
+
+
+def _rel(a, b):
+    R = b.shape[0]
+    return float(np.max(np.linalg.norm((a - b).reshape(R, -1), axis=1) / np.linalg.norm(b.reshape(R, -1), axis=1)))
+
+
+@pytest.mark.parametrize("w", SQUARE_ALL_MODES, ids=[w.name for w in SQUARE_ALL_MODES])
+def test_tensor_core_left_inverse_property_square(zl, w):
+    """Zh^- (Zh x~0) = x~0 on the tensor cores where A_m is square and all modes are kept.
+
+    x = Zh x~0 is formed by the oracle in FP64 and rounded to FP32, the library's input
+    type.  On such range-space inputs the rounding of x is amplified by cond(A_m) and by
+    (lambda_max / lambda_min)^{1/2}, so even exact arithmetic on the FP32 x misses x~0 by
+    err_ref (1e-5 to 1e-4 here).  The tensor-core path works on 22-bit operand splits
+    (FP16 hi + lo) of x and of A_m^+, about 4x coarser than FP32's 24 bits, so it must
+    recover x~0 to within a small multiple of err_ref; and it must match the oracle on
+    the same FP32 input to the mixed tolerance scaled by the same amplification.
+    """
+    Z = synth.ensemble(w).astype(np.float32)
+    lam = basis.spectrum_2d(w.Nx, w.Ny, w.ell_loc)
+    oracle = swift.Plan(Z.astype(np.float64), w.Nx, w.Ny, lam, w.tau)
+    plan = zl.zl_setup(torch.from_numpy(Z).cuda(), lam, tau=w.tau, prec="mixed", max_rhs=w.R, nx=w.Nx, ny=w.Ny)
+    assert plan.uses_tc()
+    assert plan.L == w.nh and w.nw == w.K
+    xt0 = synth.coefficients(w, plan.L)
+    x32 = np.ascontiguousarray(swift.apply_sqrt(oracle, xt0), dtype=np.float32)
+    got = zl.zl_apply_left_inverse(plan, torch.from_numpy(x32).cuda()).cpu().numpy().astype(np.float64)
+    assert plan.device_error() == 0
+    ref = swift.apply_left_inverse(oracle, x32.astype(np.float64))
+    err_ref = _rel(ref, xt0)
+    assert err_ref < 1e-3, f"the FP32 rounding of Zh x~0 alone misses x~0 by {err_ref:.2e}"
+    err_gpu = _rel(got, xt0)
+    assert err_gpu <= 16.0 * err_ref + 1e-6, f"{w.name}: {err_gpu:.3e} vs exact arithmetic {err_ref:.3e}"
+    compare.check(got, ref, max(TOL_MIXED, 16.0 * err_ref), 2, w.name)
 
 
 def test_tensor_core_repeated_calls_and_chunking(zl):
