@@ -15,12 +15,21 @@
 // exactly in the epilogue.
 //
 // A unit is ppu = floor(128 / ldp) pairs (M = ppu * ldp <= 128 rows) over all y.  Warp
-// roles (320 threads): warp 0 lane 0 = producer (one 2-D tensor copy of 32 y-rows of
-// the unit's t1 block plus the basis of those rows per stage), warp 1 = TMEM
-// allocator + MMA issuer, warps 2-5 = converters (thread = row m: FP32 -> scaled FP16
-// hi/lo A operand, 8 rows of y per slot), warps 6-9 = epilogue (TMEM -> per-pair mode
-// gather -> x~, through a shared staging tile).  Accumulators are double-buffered in
-// TMEM so the drain of unit u overlaps the MMAs of unit u + 1.  All waits are bounded.
+// roles (448 threads): warp 0 lanes 0-1 = producers (one 2-D tensor copy of 32 y-rows of
+// the unit's t1 block per stage, plus the basis of those rows when it is not resident),
+// warp 1 = TMEM allocator + MMA issuer, warps 2-9 = converters (thread = row m and half
+// of a stage: FP32 -> scaled FP16 hi/lo A operand of two 8-row slots of y), warps 10-13 =
+// epilogue (TMEM -> per-pair mode gather -> x~, through a shared staging tile).
+// Accumulators are double-buffered in TMEM so the drain of unit u overlaps the MMAs of
+// unit u + 1.
+//
+// The conversion is this kernel's bottleneck (a chain of dependent instructions per
+// value, measured: the ring depth of t1 stages does not change the kernel's time), so it
+// runs on eight warps, two per scheduler, with one proxy fence per stage.  A stage
+// returns to the producers as soon as the converters have read it (the MMAs read only
+// the converted A slots and the basis).  Both K-chunks of an MMA's B operand are the same
+// 8 y-rows of the basis, so the basis is stored once and its descriptor steps 0 bytes
+// from one K-chunk to the next.  All waits are bounded.
 
 #include "zl_internal.cuh"
 #include "tc_ptx.cuh"
@@ -51,16 +60,22 @@ using namespace tc;
 constexpr int YC = 32;                  // rows of y per stage (one tensor copy)
 constexpr int YB = 8;                   // rows of y per MMA (one A slot)
 constexpr int S = 4;                    // stage ring depth
-constexpr int SA = 2 * (YC / YB);       // A slots: two groups of one stage's 8-row blocks
-constexpr int kThreads = 320;
-constexpr int kConvWarp0 = 2, kEpiWarp0 = 6;
+constexpr int AG = 4;                   // A groups (one stage's four 8-row slots each)
+constexpr int SA = AG * (YC / YB);      // A slots
+constexpr int NE = 4;                   // ring of the commits that free A groups (one per two stages)
+constexpr int kThreads = 448;
+constexpr int kConvWarp0 = 2, kEpiWarp0 = 10;   // 8 converter warps: rows 0-127 x stage halves
 constexpr uint32_t kTmemCols = 256;     // two accumulators of up to 128 columns
 constexpr uint32_t kASlot = 4096;       // 128 rows x 32 B
 constexpr float kBasisScale = 16.0f;
 constexpr unsigned long long kWaitCycles = 4000000000ull;
 
-enum { B_FULL = 0, B_EMPTY = B_FULL + S, B_AFULL = B_EMPTY + S, B_DFULL = B_AFULL + SA,
-       B_DEMPTY = B_DFULL + 2, B_GFULL = B_DEMPTY + 2, B_GFREE, B_BASIS, B_FIN, B_COUNT };
+// B_FULL: a stage's copies landed; B_TEMPTY: the stage may be refilled (its converters have
+// read it, and the MMAs too when the stage carries the basis); B_EMPTY: commit c, issued after
+// stage 2c + 1, i.e. the MMAs of every stage up to 2c + 1 completed (frees their A groups);
+// B_AFULL: one per A group and stage half (slots 2h, 2h + 1), filled by the half's 4 warps
+enum { B_FULL = 0, B_TEMPTY = B_FULL + S, B_EMPTY = B_TEMPTY + S, B_AFULL = B_EMPTY + NE,
+       B_DFULL = B_AFULL + 2 * AG, B_DEMPTY = B_DFULL + 2, B_GFULL = B_DEMPTY + 2, B_GFREE, B_BASIS, B_FIN, B_COUNT };
 
 struct Plan {
     uint32_t stage_t, stage_b, stage, ring, basis, aring, gather, bars, total;
@@ -68,15 +83,16 @@ struct Plan {
 
 // rows_u = ppu * ldp rows of t1 per stage row of y; nb = N = 2 * pyb.  resident > 0: the
 // basis of all `resident` stages of y stays in shared memory (loaded once per CTA) and a
-// stage holds t1 only; resident == 0: every stage carries its rows of the basis.
+// stage holds t1 only; resident == 0: every stage carries its rows of the basis (per
+// 8-row block of y: nb rows x 16 B, one K-chunk).
 __host__ __device__ inline Plan smem_plan(int rows_u, int nb, int resident) {
     Plan s{};
     s.stage_t = ((uint32_t)rows_u * YC * 4u + 1023u) & ~1023u;
-    s.stage_b = (uint32_t)(YC / YB) * (uint32_t)nb * 32u;
+    s.stage_b = (uint32_t)(YC / YB) * (uint32_t)nb * 16u;
     s.stage = resident > 0 ? s.stage_t : (s.stage_t + s.stage_b + 1023u) & ~1023u;
     uint32_t o = 0;
     s.ring = o;
-    o += S * s.stage;
+    o += (uint32_t)S * s.stage;
     s.basis = o;
     o += (uint32_t)resident * s.stage_b;
     o = (o + 1023u) & ~1023u;
@@ -152,9 +168,10 @@ fwd_ypass_tc_kernel(const __grid_constant__ CUtensorMap tmap_t, const __half* __
     if (tid == 0) {
         for (int i = 0; i < S; ++i) {
             mbar_init(&bars[B_FULL + i], 1);
-            mbar_init(&bars[B_EMPTY + i], 1);
+            mbar_init(&bars[B_TEMPTY + i], resident ? 8 : 9);   // converter warps (+ the MMA commit)
         }
-        for (int i = 0; i < SA; ++i) mbar_init(&bars[B_AFULL + i], 128);
+        for (int i = 0; i < NE; ++i) mbar_init(&bars[B_EMPTY + i], 1);
+        for (int i = 0; i < 2 * AG; ++i) mbar_init(&bars[B_AFULL + i], 4);
         for (int i = 0; i < 2; ++i) {
             mbar_init(&bars[B_DFULL + i], 1);
             mbar_init(&bars[B_DEMPTY + i], 128);
@@ -186,13 +203,16 @@ fwd_ypass_tc_kernel(const __grid_constant__ CUtensorMap tmap_t, const __half* __
                              &bars[B_BASIS]);
             }
             uint32_t sc = 0, mine = 0;
-            for (int ui = 0; ui < my_units && !*abort_flag; ++ui) {
+            constexpr uint32_t S2 = (uint32_t)S;
+            bool go = true;
+            for (int ui = 0; ui < my_units && go && !*abort_flag; ++ui) {
                 const int u = (int)blockIdx.x + ui * (int)gridDim.x;
                 for (int st = 0; st < nstage_y; ++st, ++sc) {
                     if ((int)(sc & 1u) != lane) continue;
-                    const uint32_t s = sc % S;
-                    if (sc >= S && !wait_bar(&bars[B_EMPTY + s], ((sc / S) - 1) & 1u, abort_flag)) {
+                    const uint32_t s = sc % S2;
+                    if (sc >= S2 && !wait_bar(&bars[B_TEMPTY + s], ((sc / S2) - 1) & 1u, abort_flag)) {
                         fail(abort_flag, err, 1);
+                        go = false;
                         break;
                     }
                     uint8_t* dst = smem + sp.ring + s * sp.stage;
@@ -203,14 +223,15 @@ fwd_ypass_tc_kernel(const __grid_constant__ CUtensorMap tmap_t, const __half* __
                     ++mine;
                 }
             }
-            // every copy this lane issued lands before the CTA exits: its copies are the stages
-            // lane + 2 i (i < mine), alternating between its two slots, so the last two are the
-            // last ones into each of them
-            static_assert(S == 4, "two slots per issuing lane");
-            for (uint32_t i = mine > 2 ? mine - 2 : 0; i < mine; ++i) {
+            // every copy this lane issued lands before the CTA exits.  Its copies are the stages
+            // lane + 2 i (i < mine); S is even, so they all go to the slots of the lane's parity,
+            // and the last copy into each such slot is one of its last S / 2.
+            static_assert(S % 2 == 0, "two issuing lanes");
+            constexpr uint32_t half = S2 / 2u;
+            for (uint32_t i = mine > half ? mine - half : 0; i < mine; ++i) {
                 const uint32_t c = (uint32_t)lane + 2u * i;
                 const long long t0 = clock64();
-                while (!mbar_try_wait(&bars[B_FULL + c % S], (c / S) & 1u) &&
+                while (!mbar_try_wait(&bars[B_FULL + c % S2], (c / S2) & 1u) &&
                        (unsigned long long)(clock64() - t0) < kWaitCycles) {}
             }
             if (resident && lane == 0) {
@@ -223,8 +244,10 @@ fwd_ypass_tc_kernel(const __grid_constant__ CUtensorMap tmap_t, const __half* __
         if (lane == 0) {
             constexpr uint32_t idesc = idesc_f16_f32(128, NB);
             const uint64_t dA0 = smem_desc(smem_u32(smem + sp.aring), 128u, 256u);
-            const uint64_t dB0 = resident ? smem_desc(smem_u32(smem + sp.basis), 128u, 256u)
-                                          : smem_desc(smem_u32(smem + sp.ring + sp.stage_t), 128u, 256u);
+            // B: both K-chunks ([b | b] against [T_hi | T_lo]) are the same core matrices, so the
+            // K-direction stride is 0; 8-row groups of N are 128 B apart
+            const uint64_t dB0 = resident ? smem_desc(smem_u32(smem + sp.basis), 0u, 128u)
+                                          : smem_desc(smem_u32(smem + sp.ring + sp.stage_t), 0u, 128u);
             bool ok = true;
             if (resident && !wait_bar(&bars[B_BASIS], 0, abort_flag)) ok = false;
             uint32_t sc = 0;
@@ -233,20 +256,27 @@ fwd_ypass_tc_kernel(const __grid_constant__ CUtensorMap tmap_t, const __half* __
                 if (ui >= 2 && !wait_bar(&bars[B_DEMPTY + d], ((ui >> 1) - 1) & 1u, abort_flag)) { ok = false; break; }
                 tc_fence_after();
                 for (int st = 0; st < nstage_y && ok; ++st, ++sc) {
-                    const uint32_t s = sc % S;
-                    if (!wait_bar(&bars[B_FULL + s], (sc / S) & 1u, abort_flag)) { ok = false; break; }
-                    for (int b = 0; b < YC / YB; ++b) {
-                        // A group sc % 2 (slots a) is refilled once the commit of stage sc - 2 has arrived
-                        const uint32_t a = (sc & 1u) * (YC / YB) + (uint32_t)b;
-                        if (!wait_bar(&bars[B_AFULL + a], (sc >> 1) & 1u, abort_flag)) { ok = false; break; }
+                    const uint32_t s = sc % S, g = sc % AG;
+                    if (!resident && !wait_bar(&bars[B_FULL + s], (sc / S) & 1u, abort_flag)) { ok = false; break; }
+                    const uint32_t boff = resident ? (uint32_t)st * sp.stage_b : s * sp.stage;
+                    for (int hh = 0; hh < 2 && ok; ++hh) {
+                        if (!wait_bar(&bars[B_AFULL + 2 * g + (uint32_t)hh], (sc / AG) & 1u, abort_flag)) { ok = false; break; }
                         tc_fence_after();
-                        const uint64_t da = dA0 + ((a * kASlot) >> 4);
-                        const uint32_t boff = resident ? (uint32_t)st * sp.stage_b : s * sp.stage;
-                        const uint64_t db = dB0 + ((boff + (uint32_t)b * NB * 32u) >> 4);
-                        mma_f16(tbase + d * 128u, da, db, idesc, (st > 0 || b > 0) ? 1u : 0u);
+#pragma unroll
+                        for (int bb = 0; bb < 2; ++bb) {
+                            const int b = 2 * hh + bb;
+                            const uint32_t a = g * (YC / YB) + (uint32_t)b;
+                            const uint64_t da = dA0 + ((a * kASlot) >> 4);
+                            const uint64_t db = dB0 + ((boff + (uint32_t)b * NB * 16u) >> 4);
+                            mma_f16(tbase + d * 128u, da, db, idesc, (st > 0 || b > 0) ? 1u : 0u);
+                        }
                     }
-                    // one commit per stage frees its T block, its basis and its A group
-                    if (ok) mma_commit(&bars[B_EMPTY + s]);
+                    // a commit after every second stage frees the A groups of both; a stage
+                    // carrying the basis is freed by a commit of its own
+                    if (ok) {
+                        if (sc & 1u) mma_commit(&bars[B_EMPTY + (sc >> 1) % NE]);
+                        if (!resident) mma_commit(&bars[B_TEMPTY + s]);
+                    }
                 }
                 if (ok) mma_commit(&bars[B_DFULL + d]);
             }
@@ -256,8 +286,10 @@ fwd_ypass_tc_kernel(const __grid_constant__ CUtensorMap tmap_t, const __half* __
             while (!mbar_try_wait(&bars[B_FIN], 0) && (unsigned long long)(clock64() - t0) < kWaitCycles) {}
         }
     } else if (warp < kEpiWarp0) {
-        // ------------------------------------------------------------ converters: row m
-        const int m = tid - 32 * kConvWarp0;                      // 0 .. 127
+        // ------------------------------------------------------------ converters: row m, stage half h
+        const int ct = tid - 32 * kConvWarp0;                     // 0 .. 255
+        const int m = ct & 127;                                    // row of the A operand
+        const int h = ct >> 7;                                     // slots 2h, 2h + 1 of each stage
         int e2 = 0;
         (void)frexpf(__uint_as_float(*t1max), &e2);
         e2 = max(-100, min(100, e2));
@@ -268,33 +300,46 @@ fwd_ypass_tc_kernel(const __grid_constant__ CUtensorMap tmap_t, const __half* __
             for (int st = 0; st < nstage_y && ok; ++st, ++sc) {
                 const uint32_t s = sc % S;
                 if (!warp_wait_bar(&bars[B_FULL + s], (sc / S) & 1u, abort_flag)) { ok = false; break; }
-                // A group sc % 2 was last read by the MMAs of stage sc - 2
-                if (sc >= 2) {
-                    const uint32_t sp2 = sc - 2;
-                    if (!warp_wait_bar(&bars[B_EMPTY + sp2 % S], (sp2 / S) & 1u, abort_flag)) { ok = false; break; }
+                // A group sc % AG was last read by the MMAs of stage sc - AG, which commit
+                // (sc - AG) / 2 covers
+                if (sc >= (uint32_t)AG) {
+                    const uint32_t c = (sc - AG) >> 1;
+                    if (!warp_wait_bar(&bars[B_EMPTY + c % NE], (c / NE) & 1u, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
                 }
                 const float* tt = reinterpret_cast<const float*>(smem + sp.ring + s * sp.stage);
-                for (int b = 0; b < YC / YB; ++b) {
-                    const uint32_t a = (sc & 1u) * (YC / YB) + (uint32_t)b;
-                    if (m < rows_u) {
+                const uint32_t g = sc % AG;
+                const uint32_t a0 = g * (YC / YB) + 2u * (uint32_t)h;
+                if (m < rows_u) {
+#pragma unroll
+                    for (int bb = 0; bb < 2; ++bb) {
+                        const int b = 2 * h + bb;
                         float v[YB];
 #pragma unroll
                         for (int e = 0; e < YB; ++e) v[e] = tt[(b * YB + e) * rows_u + m] * ts;
                         uint32_t hi[4], lo[4];
 #pragma unroll
                         for (int e = 0; e < 4; ++e) {
-                            const __half2 h = __floats2half2_rn(v[2 * e], v[2 * e + 1]);
-                            const float2 hf = __half22float2(h);
+                            const __half2 hh = __floats2half2_rn(v[2 * e], v[2 * e + 1]);
+                            const float2 hf = __half22float2(hh);
                             const __half2 l = __floats2half2_rn(v[2 * e] - hf.x, v[2 * e + 1] - hf.y);
-                            hi[e] = *reinterpret_cast<const uint32_t*>(&h);
+                            hi[e] = *reinterpret_cast<const uint32_t*>(&hh);
                             lo[e] = *reinterpret_cast<const uint32_t*>(&l);
                         }
-                        uint8_t* dst = smem + sp.aring + a * kASlot + (m >> 3) * 256u + (m & 7) * 16u;
+                        uint8_t* dst = smem + sp.aring + (a0 + (uint32_t)bb) * kASlot + (m >> 3) * 256u + (m & 7) * 16u;
                         *reinterpret_cast<uint4*>(dst) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
                         *reinterpret_cast<uint4*>(dst + 128u) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
                     }
-                    fence_proxy_async_smem();
-                    mbar_arrive(&bars[B_AFULL + a]);
+                }
+                // this thread's A rows are written and its reads of the stage done: one proxy
+                // fence for both slots, then one arrival per warp
+                fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) {
+                    mbar_arrive(&bars[B_AFULL + 2 * g + (uint32_t)h]);
+                    mbar_arrive(&bars[B_TEMPTY + s]);
                 }
             }
         }
@@ -424,7 +469,9 @@ zl_status ytc_prepare(zl_plan_s& p, int ldp, cudaStream_t s) {
             if (used[q]) pylist.push_back(q);
     }
     const size_t yblocks = (size_t)t->nstage_y * (YC / YB);
-    const size_t per_block = (size_t)nb * 16;                       // FP16 elements per 8-row block
+    // per 8-row block of y: nb rows (b_hi rows, then b_lo rows) x 8 FP16 values of y, in 8-row
+    // core matrices of 128 B (one K-chunk; the MMA reads it for both of its K-chunks)
+    const size_t per_block = (size_t)nb * 8;                        // FP16 elements per 8-row block
     std::vector<__half> img(yblocks * per_block, __float2half_rn(0.f));
     for (size_t yb = 0; yb < yblocks; ++yb)
         for (int n = 0; n < nb; ++n) {
@@ -435,11 +482,8 @@ zl_status ytc_prepare(zl_plan_s& p, int ldp, cudaStream_t s) {
                 if (y < p.d.ny && i < (int)pylist.size()) b = kBasisScale * by_value(p.d.ny, pylist[i], y);
                 const __half hi = __double2half(b);
                 const __half v = part == 0 ? hi : __double2half(b - (double)__half2float(hi));
-                for (int c = 0; c < 2; ++c) {
-                    const size_t off = yb * per_block * 2 + (size_t)(n >> 3) * 256 + (size_t)c * 128 + (size_t)(n & 7) * 16 +
-                                       (size_t)e * 2;
-                    img[off / 2] = v;
-                }
+                const size_t off = yb * per_block * 2 + (size_t)(n >> 3) * 128 + (size_t)(n & 7) * 16 + (size_t)e * 2;
+                img[off / 2] = v;
             }
         }
     cudaError_t e = zl::dev_malloc((void**)&t->bimg, img.size() * sizeof(__half));
