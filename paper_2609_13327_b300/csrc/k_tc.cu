@@ -116,8 +116,7 @@ enum {
     B_PFULL = 0,
     B_XFULL = B_PFULL + SPH,
     B_XEMPTY = B_XFULL + SX,
-    B_BXFULL = B_XEMPTY + SX,
-    B_V1DONE = B_BXFULL + SB,
+    B_V1DONE = B_XEMPTY + SX,
     B_XLAST = B_V1DONE + kDoneV,
     B_B1FULL,                          // two slots: the B operand of group g lives in slot g % 2
     B_D1EMPTY = B_B1FULL + 2,
@@ -162,9 +161,11 @@ __host__ __device__ constexpr SmemPlan smem_plan(int nwp) {
 }
 static_assert(smem_plan(32).total <= 232448, "shared memory plan exceeds 227 KB");
 
-// Bounded wait.  The fast path (phase already complete) is one try_wait; the clock and the
+// Bounded wait.  The fast path (phase already complete) is one non-blocking test_wait
+// (measured cheaper than a try_wait on a completed phase); then try_wait, and the clock and the
 // abort flag are looked at only every 1024 polls, so waits cost the single-thread roles little.
 __device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+    if (mbar_test_wait(bar, parity)) return true;   // completed phases: the non-blocking test is cheaper
     if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
     for (uint32_t i = 1;; ++i) {
@@ -245,7 +246,6 @@ fwd_column_tc_kernel(const __grid_constant__ CUtensorMap tmap_x, const __half* _
             mbar_init(&bars[B_XFULL + i], 1);
             mbar_init(&bars[B_XEMPTY + i], kEpiThreads);
         }
-        for (int i = 0; i < SB; ++i) mbar_init(&bars[B_BXFULL + i], 1);
         for (int i = 0; i < kDoneV; ++i) mbar_init(&bars[B_V1DONE + i], 1);
         mbar_init(&bars[B_XLAST], 1);
         mbar_init(&bars[B_B1FULL], kEpiThreads);
@@ -283,13 +283,16 @@ fwd_column_tc_kernel(const __grid_constant__ CUtensorMap tmap_x, const __half* _
                     const uint32_t np = n - SPH;
                     if (!wait_bar(&bars[B_V1DONE + np % kDoneV], (np / kDoneV) & 1u, abort_flag)) { fail(abort_flag, err, 1); break; }
                 }
-                if ((n & 1u) == 0) {
+                // the basis of group gi lands on the image barrier of half-group 2gi: V1(2gi) waits
+                // for that phase before the x-pass of group gi is issued, so the x-pass needs no
+                // wait of its own
+                const bool with_basis = (n & 1u) == 0;
+                mbar_arrive_expect_tx(&bars[B_PFULL + ps], PSLOT + (with_basis ? kBxStage : 0u));
+                if (with_basis) {
                     const uint32_t bs = bc % SB;
-                    mbar_arrive_expect_tx(&bars[B_BXFULL + bs], kBxStage);
-                    bulk_g2s(sbxring + bs * kBxStage, bximg + (size_t)(gi % G) * kBxStage, kBxStage, &bars[B_BXFULL + bs]);
+                    bulk_g2s(sbxring + bs * kBxStage, bximg + (size_t)(gi % G) * kBxStage, kBxStage, &bars[B_PFULL + ps]);
                     ++bc;
                 }
-                mbar_arrive_expect_tx(&bars[B_PFULL + ps], PSLOT);
                 const size_t col = (size_t)(y + y0) * nx + (size_t)(gi % G) * GC + (n & 1u) * HG;
                 bulk_g2s(spring + ps * PSLOT, pimg + col * 128u * nwp, PSLOT, &bars[B_PFULL + ps]);
                 ++pc;
@@ -303,7 +306,6 @@ fwd_column_tc_kernel(const __grid_constant__ CUtensorMap tmap_x, const __half* _
             }
             // every issued copy must land before the CTA exits
             for (uint32_t s = 0; s < SPH; ++s) drain_slot(&bars[B_PFULL + s], pc, s, SPH);
-            for (uint32_t s = 0; s < SB; ++s) drain_slot(&bars[B_BXFULL + s], bc, s, SB);
         }
     } else if (warp == kXWarp) {
         // ------------------------------------------------------------ producer: x tiles
@@ -342,7 +344,8 @@ fwd_column_tc_kernel(const __grid_constant__ CUtensorMap tmap_x, const __half* _
             // V1 of half-group n (columns 4(n % 2) .. +3 of group n / 2) into the D1 columns
             auto v1 = [&](uint32_t n) -> bool {
                 const uint32_t g = n >> 1, h = n & 1u;
-                if (!wait_bar(&bars[B_B1FULL + (g & 1u)], (g >> 1) & 1u, abort_flag)) return false;
+                // the B operand of group g serves both half-groups: its wait is done once
+                if (h == 0 && !wait_bar(&bars[B_B1FULL + (g & 1u)], (g >> 1) & 1u, abort_flag)) return false;
                 if (!wait_bar(&bars[B_D1EMPTY], (n & 1u) ^ 1u, abort_flag)) return false;
                 tc_fence_after();
                 const uint64_t db = dB0 + (((g & 1u) * B1SLOT + h * HG * B1S) >> 4);
@@ -362,10 +365,9 @@ fwd_column_tc_kernel(const __grid_constant__ CUtensorMap tmap_x, const __half* _
             };
             // x-pass of group gi (W, the basis stage and, first group of a unit, the drained D2)
             auto xpass = [&](uint32_t gi) -> bool {
-                const uint32_t bs = gi % SB, bph = (gi / SB) & 1u;
+                const uint32_t bs = gi % SB;
                 const bool first = (gi % G) == 0;
                 if (!wait_bar(&bars[B_WFULL], gi & 1u, abort_flag)) return false;
-                if (!wait_bar(&bars[B_BXFULL + bs], bph, abort_flag)) return false;
                 if (first && !wait_bar(&bars[B_D2EMPTY], ((gi / G) & 1u) ^ 1u, abort_flag)) return false;
                 tc_fence_after();
                 const uint64_t db0 = dX0 + ((bs * kBxStage) >> 4);   // K-chunks [b_hi | b_hi]

@@ -108,6 +108,7 @@ __host__ __device__ inline Plan smem_plan(int rows_u, int nb, int resident) {
 }
 
 __device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+    if (mbar_test_wait(bar, parity)) return true;   // completed phases: the non-blocking test is cheaper
     if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
     for (uint32_t i = 1;; ++i) {
