@@ -44,15 +44,19 @@
 // in one 3-D tensor-map load, the basis of a group in one 2.3 KB copy, and one
 // L2 prefetch per group warms the images needed two groups later.
 //
-// Warp roles (352 threads): warp 0 lane 0 = producer of the pseudo-inverse
+// Warp roles (384 threads): warp 0 lane 0 = producer of the pseudo-inverse
 // images and of the per-group x-pass basis, warp 1 lane 0 = producer of the x
-// tiles, warp 2 = TMEM allocator + single-thread MMA issuer (warp w issues on
-// scheduler w % 4, which it shares with the two lighter W_c epilogue warps), warps
-// 3-10 = converters (x tile -> FP16 [x_hi; x_lo] B operand, two group slots)
-// and epilogue (TMEM -> W; TMEM -> intermediate t1 [ny][R][K][pxp]); two
-// epilogue warps share each TMEM lane quarter and split the unit's right-hand
-// sides.  All waits are bounded; on timeout the kernel
-// records an error code, drains its own copies, frees TMEM and returns.
+// tiles, warp 2 = TMEM allocator + single-thread issuer of the V1 MMAs, warp 11 lane
+// 0 = single-thread issuer of the x-pass MMAs (warp w issues on scheduler w % 4;
+// schedulers 2 and 3 are shared with the lighter W_c epilogue warps), warps 3-10 =
+// converters (x tile -> FP16 [x_hi; x_lo] B operand, two group slots) and epilogue
+// (TMEM -> W; TMEM -> intermediate t1 [ny][R][K][pxp]); two epilogue warps share each
+// TMEM lane quarter and split the unit's right-hand sides.  The two issuers wait only
+// for their own operands (measured: a single issuer spent about a third of each group
+// in waits, fences and commits while the tensor pipe ran dry), so one issues while the
+// other waits; their MMAs write disjoint TMEM columns (D1 and D2), and each commits
+// its own completions.  All waits are bounded; on timeout the kernel records an error
+// code, drains its own copies, frees TMEM and returns.
 
 #include "zl_internal.cuh"
 #include "tc_ptx.cuh"
@@ -88,12 +92,12 @@ constexpr int MT = 8;                  // x-pass M tiles: 64 members x 16 rhs / 
 constexpr int SPH = 3;                 // P image ring depth in half-groups (4 images per slot)
 constexpr int SX = 2;                  // x tile ring depth
 constexpr int SB = 3;                  // x-pass basis ring depth
-static_assert(SB == SPH, "one completion wait covers an image slot and a basis stage");
 constexpr int NEPI = 8;                // epilogue / converter warps
-constexpr int kEpiWarp0 = 3;           // warps 0: P/basis producer, 1: x producer, 2: MMA
+constexpr int kEpiWarp0 = 3;           // warps 0: P/basis producer, 1: x producer, 2: V1 MMA
 constexpr int kMmaWarp = 2;
 constexpr int kXWarp = 1;
-constexpr int kThreadsTc = 32 * kEpiWarp0 + 32 * NEPI;
+constexpr int kXpassWarp = kEpiWarp0 + NEPI;   // 11: x-pass MMA issuer
+constexpr int kThreadsTc = 32 * (kXpassWarp + 1);
 constexpr int kEpiThreads = 32 * NEPI;
 constexpr uint32_t kD1Col = MT * N2;   // 384: V1 accumulators after the x-pass accumulators
 constexpr uint32_t kTmemCols = 512;
@@ -104,21 +108,22 @@ constexpr uint32_t kBxChunk = 768;     // one K-chunk of the x-pass basis: 48 ro
 constexpr uint32_t kBxStage = 3 * kBxChunk;   // chunks: b_hi, b_hi, b_lo
 constexpr unsigned long long kWaitCycles = 4000000000ull;   // ~2 s at 2 GHz
 
-// Completion ring.  The MMA thread commits once per V1 half-group n (V1DONE, slot n % kDoneV);
-// the commit of half-group 2g + 1 also covers the x-pass of group g - 1, issued before it.
-// Every consumer that must know "V1 of half-group n (and everything issued earlier) has
-// completed" waits there; a waiter never lags the newest commit by a full ring (the producer
-// lags by at most two half-groups, the epilogue by at most one), so the phase parity is
-// unambiguous.  The x-pass of a CTA's last group, issued after its last V1, commits to XLAST.
+// Completion rings.  The V1 issuer commits once per V1 half-group n (V1DONE, slot n % kDoneV),
+// the x-pass issuer once per group g (XDONE, slot g % kDoneX: W is free, the basis stage is
+// free, and a unit that ended at group g has its whole row in D2).  A waiter never lags the
+// newest commit by a full ring (the V1 issuer runs at most one group ahead of the x-pass, the
+// producer and the epilogue at most SB groups behind it), so the phase parity is unambiguous.
 constexpr int kDoneV = 8;
+constexpr int kDoneX = 8;
 constexpr uint32_t kL2Ahead = 2;       // groups between an L2 prefetch and the shared-memory load
 enum {
     B_PFULL = 0,
     B_XFULL = B_PFULL + SPH,
     B_XEMPTY = B_XFULL + SX,
-    B_V1DONE = B_XEMPTY + SX,
-    B_XLAST = B_V1DONE + kDoneV,
-    B_B1FULL,                          // two slots: the B operand of group g lives in slot g % 2
+    B_BXFULL = B_XEMPTY + SX,          // x-pass basis stages
+    B_V1DONE = B_BXFULL + SB,
+    B_XDONE = B_V1DONE + kDoneV,
+    B_B1FULL = B_XDONE + kDoneX,       // two slots: the B operand of group g lives in slot g % 2
     B_D1EMPTY = B_B1FULL + 2,
     B_WFULL,
     B_D2EMPTY,
@@ -246,15 +251,16 @@ fwd_column_tc_kernel(const __grid_constant__ CUtensorMap tmap_x, const __half* _
             mbar_init(&bars[B_XFULL + i], 1);
             mbar_init(&bars[B_XEMPTY + i], kEpiThreads);
         }
+        for (int i = 0; i < SB; ++i) mbar_init(&bars[B_BXFULL + i], 1);
         for (int i = 0; i < kDoneV; ++i) mbar_init(&bars[B_V1DONE + i], 1);
-        mbar_init(&bars[B_XLAST], 1);
+        for (int i = 0; i < kDoneX; ++i) mbar_init(&bars[B_XDONE + i], 1);
         mbar_init(&bars[B_B1FULL], kEpiThreads);
         mbar_init(&bars[B_B1FULL + 1], kEpiThreads);
         mbar_init(&bars[B_D1EMPTY], kEpiThreads);
         mbar_init(&bars[B_WFULL], kEpiThreads);
         mbar_init(&bars[B_D2EMPTY], kEpiThreads);
         mbar_init(&bars[B_STG], kEpiThreads);
-        mbar_init(&bars[B_FIN], 1);
+        mbar_init(&bars[B_FIN], 2);            // one commit per issuer
         *abort_flag = 0;
         fence_mbar_init();
         prefetch_tmap(&tmap_x);
@@ -276,23 +282,23 @@ fwd_column_tc_kernel(const __grid_constant__ CUtensorMap tmap_x, const __half* _
                 const int u = (int)blockIdx.x + (int)(gi / G) * (int)gridDim.x;
                 const int y = u / n_rc;
                 // image slot n % SPH was last used by V1 of half-group n - SPH; for even n = 2gi the
-                // same commit covers the x-pass of group gi - SB (SB == SPH), the last user of the
-                // basis stage gi % SB
+                // basis stage gi % SB was last used by the x-pass of group gi - SB
                 const uint32_t ps = n % SPH;
                 if (n >= SPH) {
                     const uint32_t np = n - SPH;
                     if (!wait_bar(&bars[B_V1DONE + np % kDoneV], (np / kDoneV) & 1u, abort_flag)) { fail(abort_flag, err, 1); break; }
                 }
-                // the basis of group gi lands on the image barrier of half-group 2gi: V1(2gi) waits
-                // for that phase before the x-pass of group gi is issued, so the x-pass needs no
-                // wait of its own
-                const bool with_basis = (n & 1u) == 0;
-                mbar_arrive_expect_tx(&bars[B_PFULL + ps], PSLOT + (with_basis ? kBxStage : 0u));
-                if (with_basis) {
+                if ((n & 1u) == 0) {
                     const uint32_t bs = bc % SB;
-                    bulk_g2s(sbxring + bs * kBxStage, bximg + (size_t)(gi % G) * kBxStage, kBxStage, &bars[B_PFULL + ps]);
+                    if (gi >= (uint32_t)SB) {
+                        const uint32_t gp = gi - SB;
+                        if (!wait_bar(&bars[B_XDONE + gp % kDoneX], (gp / kDoneX) & 1u, abort_flag)) { fail(abort_flag, err, 1); break; }
+                    }
+                    mbar_arrive_expect_tx(&bars[B_BXFULL + bs], kBxStage);
+                    bulk_g2s(sbxring + bs * kBxStage, bximg + (size_t)(gi % G) * kBxStage, kBxStage, &bars[B_BXFULL + bs]);
                     ++bc;
                 }
+                mbar_arrive_expect_tx(&bars[B_PFULL + ps], PSLOT);
                 const size_t col = (size_t)(y + y0) * nx + (size_t)(gi % G) * GC + (n & 1u) * HG;
                 bulk_g2s(spring + ps * PSLOT, pimg + col * 128u * nwp, PSLOT, &bars[B_PFULL + ps]);
                 ++pc;
@@ -306,6 +312,7 @@ fwd_column_tc_kernel(const __grid_constant__ CUtensorMap tmap_x, const __half* _
             }
             // every issued copy must land before the CTA exits
             for (uint32_t s = 0; s < SPH; ++s) drain_slot(&bars[B_PFULL + s], pc, s, SPH);
+            for (uint32_t s = 0; s < SB; ++s) drain_slot(&bars[B_BXFULL + s], bc, s, SB);
         }
     } else if (warp == kXWarp) {
         // ------------------------------------------------------------ producer: x tiles
@@ -329,28 +336,24 @@ fwd_column_tc_kernel(const __grid_constant__ CUtensorMap tmap_x, const __half* _
             for (uint32_t s = 0; s < SX; ++s) drain_slot(&bars[B_XFULL + s], xc, s, SX);
         }
     } else if (warp == kMmaWarp) {
-        // ------------------------------------------------------------ MMA issuer
+        // ------------------------------------------------------------ V1 MMA issuer
         if (lane == 0) {
             constexpr uint32_t idesc_v1 = idesc_f16_f32(128, N1);
-            constexpr uint32_t idesc_x = idesc_f16_f32(128, N2);
             constexpr uint32_t a_sbo = (uint32_t)(NWP / 8) * 128u;
             // Base descriptors: an operand b bytes further on is the base plus (b >> 4) in the
             // start-address field, so each MMA below costs one 64-bit add per operand.
             const uint64_t dA0 = smem_desc(smem_u32(spring), 128u, a_sbo);
             const uint64_t dB0 = smem_desc(smem_u32(sb1), 128u, b1_sbo);
-            const uint64_t dW0 = smem_desc(smem_u32(sw), kWChunk, 128u);
-            const uint64_t dX0 = smem_desc(smem_u32(sbxring), kBxChunk, 128u);
             bool ok = true;
             // V1 of half-group n (columns 4(n % 2) .. +3 of group n / 2) into the D1 columns
-            auto v1 = [&](uint32_t n) -> bool {
+            for (uint32_t n = 0; n < 2 * total_groups && ok; ++n) {
                 const uint32_t g = n >> 1, h = n & 1u;
                 // the B operand of group g serves both half-groups: its wait is done once
-                if (h == 0 && !wait_bar(&bars[B_B1FULL + (g & 1u)], (g >> 1) & 1u, abort_flag)) return false;
-                if (!wait_bar(&bars[B_D1EMPTY], (n & 1u) ^ 1u, abort_flag)) return false;
-                tc_fence_after();
+                if (h == 0 && !wait_bar(&bars[B_B1FULL + (g & 1u)], (g >> 1) & 1u, abort_flag)) { ok = false; break; }
+                if (!wait_bar(&bars[B_D1EMPTY], (n & 1u) ^ 1u, abort_flag)) { ok = false; break; }
                 const uint64_t db = dB0 + (((g & 1u) * B1SLOT + h * HG * B1S) >> 4);
                 const uint32_t ps = n % SPH;
-                if (!wait_bar(&bars[B_PFULL + ps], (n / SPH) & 1u, abort_flag)) return false;
+                if (!wait_bar(&bars[B_PFULL + ps], (n / SPH) & 1u, abort_flag)) { ok = false; break; }
                 tc_fence_after();
 #pragma unroll
                 for (int j = 0; j < HG; ++j) {
@@ -360,15 +363,27 @@ fwd_column_tc_kernel(const __grid_constant__ CUtensorMap tmap_x, const __half* _
                         mma_f16(tbase + kD1Col + (uint32_t)(j * N1), da + (uint64_t)(ks * 16),
                                 db + (uint64_t)((j * B1S + ks * 256u) >> 4), idesc_v1, ks > 0 ? 1u : 0u);
                 }
-                mma_commit(&bars[B_V1DONE + n % kDoneV]);   // D1, B1, the image slot (+ the x-pass before it)
-                return true;
-            };
+                mma_commit(&bars[B_V1DONE + n % kDoneV]);   // D1, B1, the image slot
+            }
+            if (!ok) fail(abort_flag, err, 2);
+            mma_commit(&bars[B_FIN]);
+            const long long t0 = clock64();
+            while (!mbar_try_wait(&bars[B_FIN], 0) && (unsigned long long)(clock64() - t0) < kWaitCycles) {}
+        }
+    } else if (warp == kXpassWarp) {
+        // ------------------------------------------------------------ x-pass MMA issuer
+        if (lane == 0) {
+            constexpr uint32_t idesc_x = idesc_f16_f32(128, N2);
+            const uint64_t dW0 = smem_desc(smem_u32(sw), kWChunk, 128u);
+            const uint64_t dX0 = smem_desc(smem_u32(sbxring), kBxChunk, 128u);
+            bool ok = true;
             // x-pass of group gi (W, the basis stage and, first group of a unit, the drained D2)
-            auto xpass = [&](uint32_t gi) -> bool {
+            for (uint32_t gi = 0; gi < total_groups && ok; ++gi) {
                 const uint32_t bs = gi % SB;
                 const bool first = (gi % G) == 0;
-                if (!wait_bar(&bars[B_WFULL], gi & 1u, abort_flag)) return false;
-                if (first && !wait_bar(&bars[B_D2EMPTY], ((gi / G) & 1u) ^ 1u, abort_flag)) return false;
+                if (!wait_bar(&bars[B_WFULL], gi & 1u, abort_flag)) { ok = false; break; }
+                if (first && !wait_bar(&bars[B_D2EMPTY], ((gi / G) & 1u) ^ 1u, abort_flag)) { ok = false; break; }
+                if (!wait_bar(&bars[B_BXFULL + bs], (gi / SB) & 1u, abort_flag)) { ok = false; break; }
                 tc_fence_after();
                 const uint64_t db0 = dX0 + ((bs * kBxStage) >> 4);   // K-chunks [b_hi | b_hi]
                 const uint64_t db1 = db0 + (kBxChunk >> 4);          // K-chunks [b_hi | b_lo]
@@ -379,13 +394,7 @@ fwd_column_tc_kernel(const __grid_constant__ CUtensorMap tmap_x, const __half* _
                 for (int t = 0; t < MT; ++t) mma_f16(tbase + (uint32_t)(t * N2), dw0 + ((t * 2048u) >> 4), db0, idesc_x, acc0);
 #pragma unroll
                 for (int t = 0; t < MT; ++t) mma_f16(tbase + (uint32_t)(t * N2), dw1 + ((t * 2048u) >> 4), db1, idesc_x, 1u);
-                return true;
-            };
-            for (uint32_t gi = 0; gi < total_groups && ok; ++gi)
-                ok = v1(2 * gi) && (gi == 0 || xpass(gi - 1)) && v1(2 * gi + 1);
-            if (ok && total_groups > 0) {
-                ok = xpass(total_groups - 1);
-                if (ok) mma_commit(&bars[B_XLAST]);
+                mma_commit(&bars[B_XDONE + gi % kDoneX]);   // W, the basis stage, D2 of a finished unit
             }
             if (!ok) fail(abort_flag, err, 2);
             mma_commit(&bars[B_FIN]);
@@ -535,8 +544,12 @@ fwd_column_tc_kernel(const __grid_constant__ CUtensorMap tmap_x, const __half* _
             if (g >= 1 && g + 1 < total_groups && !convert(g + 1)) { ok = false; break; }
             // ---- second half-group: columns 4-7
             if (!drain_d1(2 * g + 1, s1)) { ok = false; break; }
-            // ---- the commit just seen covers the x-pass of group g - 1: W is free, and a unit that
-            // ended at group g - 1 has its whole row in D2
+            // ---- the x-pass of group g - 1 has completed: W is free, and a unit that ended at
+            // group g - 1 has its whole row in D2
+            if (g >= 1) {
+                const uint32_t gp = g - 1;
+                if (!warp_wait_bar(&bars[B_XDONE + gp % kDoneX], (gp / kDoneX) & 1u, abort_flag)) { ok = false; break; }
+            }
             if (pending) {
                 if (!drain_d2(pending_g)) { ok = false; break; }
                 pending = false;
@@ -572,7 +585,8 @@ fwd_column_tc_kernel(const __grid_constant__ CUtensorMap tmap_x, const __half* _
             }
         }
         if (ok && pending) {
-            if (!warp_wait_bar(&bars[B_XLAST], 0, abort_flag) || !drain_d2(pending_g)) ok = false;
+            const uint32_t gp = total_groups - 1;
+            if (!warp_wait_bar(&bars[B_XDONE + gp % kDoneX], (gp / kDoneX) & 1u, abort_flag) || !drain_d2(pending_g)) ok = false;
         }
         if (!ok) fail(abort_flag, err, 3);
     }
