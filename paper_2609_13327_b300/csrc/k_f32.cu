@@ -67,17 +67,27 @@ __host__ __device__ inline FPlan fplan(int RC, int N, int nstage) {
     return f;
 }
 
-__device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
-    if (mbar_test_wait(bar, parity)) return true;   // completed phases: the non-blocking test is cheaper
-    if (mbar_try_wait(bar, parity)) return true;
+// Polling modes of a bounded wait.  The single-thread roles (producers, MMA issuers) poll with
+// the non-blocking test_wait, so they react to a completed phase within one poll; whole warps
+// use try_wait, whose suspension leaves the issue slots of their scheduler to the warps that
+// share it (polling everywhere measured no faster).
+constexpr bool kWarpSpin = false;
+
+template <bool kSpin>
+__device__ __forceinline__ bool wait_bar_t(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+    if (mbar_test_wait(bar, parity)) return true;
     const long long t0 = clock64();
     for (uint32_t i = 1;; ++i) {
-        if (mbar_try_wait(bar, parity)) return true;
+        if (kSpin ? mbar_test_wait(bar, parity) : mbar_try_wait(bar, parity)) return true;
         if ((i & 1023u) == 0u) {
             if (*abort_flag) return false;
             if ((unsigned long long)(clock64() - t0) > kWaitCycles) return false;
         }
     }
+}
+
+__device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+    return wait_bar_t<true>(bar, parity, abort_flag);
 }
 
 __device__ __forceinline__ void fail(volatile int* abort_flag, int* err, int code) {
@@ -194,7 +204,7 @@ fwd_column_f32_kernel(const __grid_constant__ CUtensorMap tmap_x, const __grid_c
                 for (int r = 0; r < RC; ++r) a[k][r] = 0.f;
             for (int g = 0; g < nlg; ++g, ++seq) {
                 const uint32_t s = seq % (uint32_t)nstage;
-                if (ok && !wait_bar(&bars[B_FULL + s], (seq / (uint32_t)nstage) & 1u, abort_flag)) {
+                if (ok && !wait_bar_t<kWarpSpin>(&bars[B_FULL + s], (seq / (uint32_t)nstage) & 1u, abort_flag)) {
                     fail(abort_flag, err, 2);
                     ok = false;
                 }
@@ -520,7 +530,7 @@ inv_column_f32_kernel(const __grid_constant__ CUtensorMap tmap_m, const float* _
             if (mc + 1 < nmc) fetch_u(y, r0, mc + 1);
             for (int g = 0; g < ngr; ++g, ++seq) {
                 const uint32_t s = seq % (uint32_t)nstage;
-                if (ok && !wait_bar(&bars[B_FULL + s], (seq / (uint32_t)nstage) & 1u, abort_flag)) {
+                if (ok && !wait_bar_t<kWarpSpin>(&bars[B_FULL + s], (seq / (uint32_t)nstage) & 1u, abort_flag)) {
                     fail(abort_flag, err, 4);
                     ok = false;
                 }

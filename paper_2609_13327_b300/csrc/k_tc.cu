@@ -166,15 +166,19 @@ __host__ __device__ constexpr SmemPlan smem_plan(int nwp) {
 }
 static_assert(smem_plan(32).total <= 232448, "shared memory plan exceeds 227 KB");
 
-// Bounded wait.  The fast path (phase already complete) is one non-blocking test_wait
-// (measured cheaper than a try_wait on a completed phase); then try_wait, and the clock and the
-// abort flag are looked at only every 1024 polls, so waits cost the single-thread roles little.
-__device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
-    if (mbar_test_wait(bar, parity)) return true;   // completed phases: the non-blocking test is cheaper
-    if (mbar_try_wait(bar, parity)) return true;
+// Bounded waits.  The first poll is the non-blocking test_wait (cheaper than a try_wait on a
+// completed phase); the clock and the abort flag are looked at only every 1024 polls.  The
+// single-thread roles (producers, MMA issuers) keep polling with test_wait, so they react to a
+// completed phase within one poll; whole warps use try_wait, whose suspension leaves the issue
+// slots of their scheduler to the warps that share it (polling everywhere measured no faster).
+constexpr bool kWarpSpin = false;
+
+template <bool kSpin>
+__device__ __forceinline__ bool wait_bar_t(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+    if (mbar_test_wait(bar, parity)) return true;
     const long long t0 = clock64();
     for (uint32_t i = 1;; ++i) {
-        if (mbar_try_wait(bar, parity)) return true;
+        if (kSpin ? mbar_test_wait(bar, parity) : mbar_try_wait(bar, parity)) return true;
         if ((i & 1023u) == 0u) {
             if (*abort_flag) return false;
             if ((unsigned long long)(clock64() - t0) > kWaitCycles) return false;
@@ -182,9 +186,13 @@ __device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, volatil
     }
 }
 
+__device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+    return wait_bar_t<true>(bar, parity, abort_flag);
+}
+
 // Wait used by whole warps before warp-collective tcgen05.ld: the outcome is made warp-uniform.
 __device__ __forceinline__ bool warp_wait_bar(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
-    const bool ok = wait_bar(bar, parity, abort_flag);
+    const bool ok = wait_bar_t<kWarpSpin>(bar, parity, abort_flag);
     return __all_sync(0xffffffffu, ok);
 }
 
