@@ -22,7 +22,7 @@
 // dropping only the 2^-22 terms W_lo b_lo and W_c b_lo.  The regrouping of
 // w^(m) into member segments (steps V2-V3, the paper's inter-processor
 // exchange) thus never leaves the SM.  The y-pass, Delta^{-1/2} scaling and
-// compaction (the rest of V4, and V5) follow in the CUDA-core kernel fwd_ypass.
+// compaction (the rest of V4, and V5) follow in fwd_ypass_tc_kernel (k_ytc.cu).
 //
 // Shared-memory bandwidth (about 128 B per clock, shared by the tensor pipe's
 // operand reads, the bulk copies and the warps' loads and stores) bounds this
@@ -31,11 +31,10 @@
 //
 // TMEM: 384 columns of x-pass accumulators (8 tiles x 48) and 128 columns of
 // V1 accumulators, i.e. 4 grid columns x 32; V1 therefore runs in half-groups
-// of 4 columns.  The MMA order V1(2g), x-pass(g-1), V1(2g+1) keeps the tensor
-// pipe busy while the epilogue drains the first half-group, and because the
-// pipe completes MMAs in issue order, the commit after V1(2g+1) also reports
-// the x-pass of group g-1: the single issuing thread commits only twice per
-// group (a commit holds it for about as long as the MMAs still queued).
+// of 4 columns, and V1 of half-group n + 1 waits until the epilogue has drained
+// D1 of half-group n.  The x-pass of group g needs the W of both half-groups of
+// g, so it runs about one group behind V1 on its own issuing thread and keeps the
+// tensor pipe busy while the epilogue drains D1 and writes W.
 //
 // Operand supply: the engine behind the bulk copies spends a roughly fixed
 // time per copy, so operands arrive in few, large copies: the [P_hi; P_lo]
