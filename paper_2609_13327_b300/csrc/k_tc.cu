@@ -280,7 +280,7 @@ fwd_column_tc_kernel(const __grid_constant__ CUtensorMap tmap_x, const __half* _
 
     if (warp == 0) {
         // ------------------------------------------------------------ producer: images + x-pass basis
-        // (starve: a test of the failure path; no copy is issued, so the MMA thread's bounded
+        // (starve: a test of the failure path; no copy is issued, so the V1 issuer's bounded
         // wait for the first image runs out)
         if (lane == 0 && !starve) {
             uint32_t pc = 0, bc = 0;           // half-groups, basis stages issued
