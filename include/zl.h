@@ -59,7 +59,7 @@ typedef enum {
     ZL_ERR_ALLOC = 4,        /* cudaMalloc failed during setup                              */
     ZL_ERR_CUDA = 5,         /* a CUDA runtime call or kernel launch failed                 */
     ZL_ERR_TIMEOUT = 6,      /* a bounded device-side wait gave up                          */
-    ZL_ERR_UNSUPPORTED = 7   /* valid request that this build does not implement           */
+    ZL_ERR_UNSUPPORTED = 7   /* valid request that this library version does not implement */
 } zl_status;
 
 typedef enum {
@@ -383,7 +383,7 @@ zl_status zl_delta(zl_plan plan, const void* xt, const void* back, void* d, doub
  * The file holds the descriptor, the kept modes and their eigenvalues, the
  * rank status, the plan's copy of Z and the pseudo-inverse P (its storage
  * precision: 2 K n_w n_h elements, about 1 GB at 256x256x32, K = 64, FP32), in
- * this build's native layout (not portable across builds or byte orders).
+ * the library's native layout (not portable across library versions or byte orders).
  * zl_plan_load validates the header (magic, sizes, ascending modes, positive
  * eigenvalues) and rejects any mismatch or short file with ZL_ERR_ARG before
  * touching the device; it then builds the tables and the tensor-core operands
