@@ -1,5 +1,5 @@
 """Host logic of bench.py without a GPU: the multi-rank reduction (gloo, two CPU ranks
-under torchrun, as the driver launches the bench) and the reference arm, which runs the
+under torchrun, as a multi-GPU launch runs the bench) and the reference arm, which runs the
 FP64 oracle on the host and, under torchrun, prints from rank 0 only."""
 
 import json

@@ -45,7 +45,7 @@ def test_element_sizes():
 
 def test_bytes_per_launch_and_peak_source():
     """The 64-rhs launch of the 256x256x32 workload counts 820.9 MB; the denominator is the
-    measured copy bandwidth when the file is there, else the recipe's 6.4 TB/s."""
+    measured copy bandwidth of MEASURED_PEAKS.json when the file is there, else 6.4 TB/s."""
     w = synth.WORKLOADS["c3_256x256x32"]
     assert bench.algorithmic_bytes_per_rhs(w, 949, w.prec, w.R) * w.R == 820854784
     peak, kind = bench.measured_peak_hbm()
