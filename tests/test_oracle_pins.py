@@ -390,3 +390,66 @@ def test_gram_route_matches_svd_route():
         W2, bad = swift.gram_route_pinv_apply(plan.A, X)
         assert bad == -1
         assert np.abs(W1 - W2).max() <= 1e-11 * np.abs(W1).max()
+
+
+# ---------------------------------------------------------------- block structure of A (Sec. 3.9)
+
+def _selectors(nw, K, nh, m):
+    """Phi_m (n_w x n): picks the states (l, m); Psi_m (K x K n_h): picks the columns (k, m)."""
+    Phi = np.zeros((nw, nw * nh))
+    Phi[np.arange(nw), np.arange(nw) * nh + m] = 1.0
+    Psi = np.zeros((K, K * nh))
+    Psi[np.arange(K), np.arange(K) * nh + m] = 1.0
+    return Phi, Psi
+
+
+@pytest.mark.parametrize("w", [WIDE, TALL, SQUARE_RING], ids=["wide", "tall", "square"])
+def test_A_is_the_sum_of_its_column_blocks(w):
+    """A = sum_m Phi_m^T A_m Psi_m with A_m[l][k] = z_k at state (l, m) (Eq. ADef and the
+    column decomposition of Sec. 3.9); assembled here from the member array, not from diagonals."""
+    Z = synth.ensemble(w)
+    K, nw, nh = Z.shape
+    acc = np.zeros((nw * nh, K * nh))
+    for m in range(nh):
+        Phi, Psi = _selectors(nw, K, nh, m)
+        Am = Z[:, :, m].T                                      # n_w x K
+        acc += Phi.T @ Am @ Psi
+    assert np.array_equal(acc, dense.matrix_A(Z))
+
+
+@pytest.mark.parametrize("w", [WIDE, TALL, SQUARE_RING], ids=["wide", "tall", "square"])
+def test_block_svd_of_A(w):
+    """Per-column SVDs A_m = E_m Lambda_m F_m^T (Eq. svdOfAm) assemble into an SVD of A:
+    E = sum_m Phi_m^T E_m and F = sum_m Psi_m^T F_m have orthonormal columns, and A = E Lambda F^T."""
+    Z = synth.ensemble(w)
+    K, nw, nh = Z.shape
+    Es, Fs, Ls = [], [], []
+    for m in range(nh):
+        Phi, Psi = _selectors(nw, K, nh, m)
+        Em, lm, Fmt = np.linalg.svd(Z[:, :, m].T, full_matrices=False)
+        Es.append(Phi.T @ Em)
+        Fs.append(Psi.T @ Fmt.T)
+        Ls.append(lm)
+    E, F, lam = np.hstack(Es), np.hstack(Fs), np.concatenate(Ls)
+    g = min(nw, K)
+    assert E.shape == (nw * nh, g * nh) and F.shape == (K * nh, g * nh)
+    assert np.abs(E.T @ E - np.eye(g * nh)).max() < 1e-13
+    assert np.abs(F.T @ F - np.eye(g * nh)).max() < 1e-13
+    A = dense.matrix_A(Z)
+    assert np.abs(E @ (lam[:, None] * F.T) - A).max() < 1e-13 * np.abs(A).max()
+    # the singular values of A are those of the blocks (a library SVD of the dense A)
+    sv = np.linalg.svd(A, compute_uv=False)
+    assert np.allclose(np.sort(sv)[::-1][:g * nh], np.sort(lam)[::-1], rtol=1e-12, atol=0)
+
+
+def test_rank_is_additive_over_columns():
+    """rank(A) = sum_m rank(A_m) (Sec. 3.9, S2): one column made rank-deficient lowers the
+    rank of A by one."""
+    w = SQUARE_RING
+    Z = synth.ensemble(w).copy()
+    K, nw, nh = Z.shape
+    m0 = 5
+    Z[1, :, m0] = Z[0, :, m0]                                  # two equal members at column m0
+    ranks = [np.linalg.matrix_rank(Z[:, :, m].T) for m in range(nh)]
+    assert ranks[m0] == min(nw, K) - 1 and sum(ranks) == min(nw, K) * nh - 1
+    assert np.linalg.matrix_rank(dense.matrix_A(Z)) == sum(ranks)
